@@ -1,0 +1,461 @@
+"""Benchmark of the stable multisplit on one GB300 (or N replicas).
+
+Workload (one "step"): the multisplit sweep at n = 2^26 -- uniform and skewed
+uint32 keys with range buckets from m-1 sorted uniform splitters, m in
+{2, 8, 32, 64, 256}, keys only and key-value (value = original index), plus
+float32 keys uniform in [0, 1000) with delta buckets (delta = 1000/m), keys
+only and key-value: 30 multisplits of 2^26 elements each.  Inputs are seeded,
+synthetic, resident in HBM before the timed region, and each 256 MB input is
+larger than the 126 MB L2, so no L2 flush is needed between steps.
+
+Printed: one JSON line (rank 0).  ``value`` is the whole-job rate in 1e9
+elements per second (keys for key-only cases, pairs for key-value cases);
+``sweep`` gives every case's own Gkeys/s or Gpairs/s and its fraction of the
+compulsory-bytes HBM roofline (read once + write once: 8 B/key, 16 B/pair).
+``roofline`` is the post-scan kernel (the dominant one), timed with CUDA events
+recorded by the library around each stage on the launching stream.  ``e2e``
+runs the same sweep from pinned host buffers with the host<->device copies in
+the timed region.  ``cpu_baseline`` times the CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle (the reference arm of this
+repository) on samples of the same workload.  With N > 1 (torchrun) every
+rank runs the same sweep on its own GPU ("replicas only": multisplit needs no
+exchange step between GPUs here); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "multisplit Gkeys/s & Gpairs/s and % of HBM roofline vs m; batched vs plain; p99 ms"
+MS_LIST = [2, 8, 32, 64, 256]
+WORKLOAD = ("multisplit sweep n=2^26: uint32 keys uniform + skewed (geometric p=0.5), range buckets "
+            "(m-1 sorted uniform splitters), float32 keys uniform [0,1000) with delta=1000/m, "
+            "m in {2,8,32,64,256}, keys-only and key-value (value = index)")
+
+
+def cases(n_log2: int):
+    """(name, key_array_id, kind, m, pairs) for the 30 sweep cases."""
+    out = []
+    for dist in ("uniform", "skewed"):
+        for m in MS_LIST:
+            for pairs in (False, True):
+                out.append((f"range_{dist}_m{m}_{'pairs' if pairs else 'keys'}", (dist, m), "range", m, pairs))
+    for m in MS_LIST:
+        for pairs in (False, True):
+            out.append((f"delta_f32_m{m}_{'pairs' if pairs else 'keys'}", ("f32", m), "delta", m, pairs))
+    return out
+
+
+def make_inputs(n: int):
+    """Host arrays: key arrays by id, splitters per m, values."""
+    keys, spl = {}, {}
+    uni = synthetic.uniform_u32(n, 2026)
+    f32 = synthetic.uniform_f32_1000(n, 2027)
+    for m in MS_LIST:
+        spl[m] = synthetic.range_splitters(m, 100 + m)
+        keys[("uniform", m)] = uni
+        keys[("skewed", m)] = synthetic.skewed_u32(n, spl[m], 200 + m)
+        keys[("f32", m)] = f32
+    vals = synthetic.index_values(n)
+    return keys, spl, vals
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1701_01189_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per element of the post-scan from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "postscan_traffic.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+    except Exception:
+        return None
+    if j.get("source_hash") != kernel_source_hash():
+        return None
+    return j
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank: int, world: int):
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+    from paper_1701_01189_gb300 import metrics
+    from paper_1701_01189_gb300.build import build
+
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    ms.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 1 << args.n_log2
+    hk, hspl, hvals = make_inputs(n)
+    case_list = cases(args.n_log2)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+
+    dkeys = {}
+    for cid, arr in hk.items():
+        key = id(arr)
+        if key not in dkeys:
+            dkeys[key] = to_dev(arr)
+    dk = {cid: dkeys[id(arr)] for cid, arr in hk.items()}
+    dspl = {m: to_dev(s) for m, s in hspl.items()}
+    dvals = to_dev(hvals)
+    out_k = torch.empty(n, dtype=torch.int32, device=dev)
+    out_v = torch.empty(n, dtype=torch.int32, device=dev)
+    offs = torch.empty(257, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    specs = {}
+    for name, cid, kind, m, pairs in case_list:
+        if kind == "range":
+            specs[name] = ms.BucketSpec.range_u32(dspl[m]).c()
+        else:
+            specs[name] = ms.BucketSpec.delta_f32(m, float(np.float32(1000.0) / np.float32(m))).c()
+
+    def one(name, cid, pairs, kin, vin):
+        if pairs:
+            st = ms.ms_multisplit_pairs(kin.data_ptr(), vin.data_ptr(), n, specs[name], out_k.data_ptr(),
+                                        out_v.data_ptr(), offs.data_ptr(), sptr)
+        else:
+            st = ms.ms_multisplit_keys(kin.data_ptr(), n, specs[name], out_k.data_ptr(), offs.data_ptr(), sptr)
+        if st != ms.MS_OK:
+            raise ms.MsError(st, name)
+
+    def step(events=None):
+        for ci, (name, cid, kind, m, pairs) in enumerate(case_list):
+            if events is not None:
+                events[ci][0].record(stream)
+            one(name, cid, pairs, dk[cid], dvals)
+            if events is not None:
+                events[ci][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ms.device_status() != ms.MS_OK:
+        raise RuntimeError("device status not OK after warm-up")
+
+    # ---- timed region (device-resident inputs)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in case_list] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", torch.cuda.current_device())))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms.ms_stage_timing(1)
+    t0.record(stream)
+    for s in range(args.steps):
+        step(ev[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms.ms_stage_timing(0)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t0.elapsed_time(t1)
+    pre_ms, scan_ms, post_ms, n_ms = ms.ms_stage_times()
+    if ms.device_status() != ms.MS_OK:
+        raise RuntimeError("device status not OK after the timed region")
+
+    per_case = {}
+    for ci, (name, cid, kind, m, pairs) in enumerate(case_list):
+        tms = sum(ev[s][ci][0].elapsed_time(ev[s][ci][1]) for s in range(args.steps)) / args.steps
+        rate = metrics.rate_g(n, tms * 1e-3)
+        peak, _ = measured_peaks()
+        comp = metrics.sol_rate_g(peak, metrics.compulsory_bytes_per_element(pairs))
+        per_case[name] = {"ms": round(tms, 4), ("gpairs_s" if pairs else "gkeys_s"): round(rate, 2),
+                          "frac_compulsory_roofline": round(rate / comp, 4)}
+
+    elems_per_step = n * len(case_list)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = metrics.rate_g(elems_per_step * args.steps * world, total_ms * 1e-3)
+
+    # roofline of the post-scan kernel: algorithmic bytes = read + write of every key (and value)
+    peak, peak_kind = measured_peaks()
+    n_pairs_cases = sum(1 for c in case_list if c[4])
+    n_keys_cases = len(case_list) - n_pairs_cases
+    post_bytes = args.steps * n * (n_keys_cases * 8 + n_pairs_cases * 16)
+    achieved = post_bytes / (post_ms * 1e-3) / 1e9 if post_ms > 0 else None
+    tr = profiled_traffic()
+    roofline = {"kernel": "k_postscan", "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak, "peak_kind": f"{peak_kind} (copy bandwidth, burst)", "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": (round(tr["bytes_per_launch_full"], 0) if tr else None),
+                "algorithmic_bytes_per_launch": post_bytes / max(1, n_ms),
+                "stage_ms_per_step": {"prescan": round(pre_ms / args.steps, 4),
+                                      "scan": round(scan_ms / args.steps, 4),
+                                      "postscan": round(post_ms / args.steps, 4)}}
+
+    result = {"metric": METRIC, "value": round(value, 3), "unit": "G elements/s (keys or pairs)",
+              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+              "config": {"workload": WORKLOAD, "n": n, "cases": len(case_list),
+                         "l2": "inputs (256 MB each) larger than L2; no flush",
+                         "parallelism": "replicas" if world > 1 else "single"},
+              "gpu_launches": 3 * len(case_list) * args.steps,
+              "roofline": roofline, "sweep": per_case, "clocks": clk}
+
+    if not args.no_e2e:
+        result["e2e"] = e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(hk, hspl, hvals, case_list, n, budget_s=args.cpu_budget)
+    return result
+
+
+def e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n, world):
+    """The same sweep through the C ABI with host buffers: each case copies its keys (and
+    values) from pinned host memory, runs, and copies its outputs and offsets back."""
+    pin = {}
+    for cid, arr in hk.items():
+        if id(arr) not in pin:
+            pin[id(arr)] = torch.from_numpy(np.ascontiguousarray(arr).view(np.int32)).pin_memory()
+    hkeys = {cid: pin[id(arr)] for cid, arr in hk.items()}
+    hv = torch.from_numpy(hvals.view(np.int32)).pin_memory()
+    ho_k = torch.empty(n, dtype=torch.int32).pin_memory()
+    ho_v = torch.empty(n, dtype=torch.int32).pin_memory()
+    ho_off = torch.empty(257, dtype=torch.int32).pin_memory()
+    dk = torch.empty(n, dtype=torch.int32, device=dev)
+    dv = torch.empty(n, dtype=torch.int32, device=dev)
+    ok = torch.empty(n, dtype=torch.int32, device=dev)
+    ov = torch.empty(n, dtype=torch.int32, device=dev)
+    off = torch.empty(257, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        for name, cid, kind, m, pairs in case_list:
+            dk.copy_(hkeys[cid], non_blocking=True)
+            h2d += 4 * n
+            if pairs:
+                dv.copy_(hv, non_blocking=True)
+                h2d += 4 * n
+                st = ms.ms_multisplit_pairs(dk.data_ptr(), dv.data_ptr(), n, specs[name], ok.data_ptr(),
+                                            ov.data_ptr(), off.data_ptr(), sptr)
+            else:
+                st = ms.ms_multisplit_keys(dk.data_ptr(), n, specs[name], ok.data_ptr(), off.data_ptr(), sptr)
+            if st != ms.MS_OK:
+                raise ms.MsError(st, name)
+            ho_k.copy_(ok, non_blocking=True)
+            d2h += 4 * n
+            if pairs:
+                ho_v.copy_(ov, non_blocking=True)
+                d2h += 4 * n
+            ho_off[: m + 1].copy_(off[: m + 1], non_blocking=True)
+            d2h += 4 * (m + 1)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    steps = max(1, args.steps)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = metrics.rate_g(n * len(case_list) * steps * world, ms_total * 1e-3)
+    return {"value": round(value, 3), "unit": "G elements/s (keys or pairs)",
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(hk, hspl, hvals, case_list, sample_n: int):
+    """Runs the oracle on the first sample_n elements of every case; returns (elements, seconds)."""
+    import oracle
+
+    elems, secs = 0, 0.0
+    for name, cid, kind, m, pairs in case_list:
+        keys = hk[cid][:sample_n]
+        vals = hvals[:sample_n] if pairs else None
+        if kind == "range":
+            spec = oracle.Spec(oracle.RANGE_U32, m, splitters=hspl[m])
+        else:
+            spec = oracle.Spec(oracle.DELTA_F32, m, x0=0.0, delta=float(np.float32(1000.0) / np.float32(m)))
+        t = time.perf_counter()
+        oracle.multisplit(keys, vals, spec)
+        secs += time.perf_counter() - t
+        elems += len(keys)
+    return elems, secs
+
+
+def cpu_baseline(hk, hspl, hvals, case_list, n, budget_s: float = 15.0):
+    # calibrate the sample size so the whole sample takes about budget_s seconds
+    e, s = oracle_sample(hk, hspl, hvals, case_list, 1 << 16)
+    per_elem = s / max(1, e)
+    sample_n = int(min(n, max(1 << 16, budget_s / max(per_elem, 1e-12) / len(case_list))))
+    sample_n = 1 << max(16, int(np.floor(np.log2(sample_n))))
+    e, s = oracle_sample(hk, hspl, hvals, case_list, sample_n)
+    return {"value": round(e / s / 1e9, 5), "unit": "G elements/s (keys or pairs)", "cores": 1,
+            "kind": "oracle", "seconds": round(s, 2),
+            "sample": f"each of the {len(case_list)} sweep cases on its first {sample_n} elements "
+                      f"(single-threaded C oracle, Eq. 1 by counting)"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on bounded samples of the same workload."""
+    n = 1 << args.n_log2
+    sample_n = min(n, 1 << args.ref_sample_log2)
+    hk, hspl, hvals = make_inputs(sample_n)
+    case_list = cases(args.n_log2)
+    for _ in range(args.warmup):
+        oracle_sample(hk, hspl, hvals, case_list, sample_n)
+    e_tot, s_tot = 0, 0.0
+    for _ in range(args.steps):
+        e, s = oracle_sample(hk, hspl, hvals, case_list, sample_n)
+        e_tot += e
+        s_tot += s
+    value = e_tot / s_tot / 1e9
+    desc = (f"each step: the {len(case_list)} sweep cases on {sample_n} elements each "
+            f"(single-threaded C oracle)")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5),
+            "unit": "G elements/s (keys or pairs)", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * s_tot / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "cases": len(case_list), "sample_n": sample_n},
+            "cpu_baseline": {"value": round(value, 5), "unit": "G elements/s (keys or pairs)", "cores": 1,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 5), "unit": "G elements/s (keys or pairs)", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ms", choices=["ms", "reference"])
+    ap.add_argument("--n-log2", type=int, default=26)
+    ap.add_argument("--ref-sample-log2", type=int, default=20)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    import torch
+
+    if world > 1:
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    if args.warmup < 3:
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    res = run_gpu(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

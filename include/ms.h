@@ -1,0 +1,130 @@
+/*
+ * ms.h -- C ABI of the GB300 (sm_103a) stable multisplit library (libms.so).
+ *
+ * The operation is the multisplit primitive of "GPU Multisplit: an extended
+ * study of a parallel algorithm" (Ashkiani, Davidson, Meyer, Owens), Section
+ * 3.1: permute n 32-bit keys (or key-value pairs) into m contiguous buckets in
+ * ascending bucket-ID order, keeping the input order inside every bucket
+ * (stable), and report where every bucket starts.  The final position of
+ * element i in bucket j is Eq. 1 of Section 4.2:
+ *     p(i) = sum_{k<j} h_k + |{u_r in B_j : r < i}|.
+ * The radix sort of Section 7.1 is built from multisplit passes whose bucket
+ * identifier is the radix digit f_k(u) = (u >> kr) & (2^r - 1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_in / *_out / offsets are DEVICE pointers on the current
+ *     CUDA device, owned by the caller.  Keys and values are copied bit for
+ *     bit (float keys travel as their raw bits).  Inputs and outputs must not
+ *     overlap.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are asynchronous with respect to the host: they enqueue
+ *     work on `stream` and return.
+ *   - The library owns its scratch memory (histogram matrix, look-back status
+ *     words).  It takes it from a library-owned, stream-ordered memory pool on
+ *     the calling stream and returns it on the same stream, so a call is safe
+ *     to overlap with calls on other streams.
+ *   - Errors are status codes; nothing is thrown across the ABI.  Argument
+ *     errors are detected on the host before anything is enqueued.  A device
+ *     side failure (a bounded wait that ran out) is recorded in a per-device
+ *     status word that ms_device_status() returns.
+ *   - n may be 0 (offsets are then all 0).  n must be < 2^32.
+ */
+#ifndef MS_H_
+#define MS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_INVALID_ARG = 1,   /* a bad argument; nothing was enqueued */
+  MS_ERR_UNSUPPORTED = 2,   /* a valid request this build does not handle */
+  MS_ERR_OUT_OF_MEMORY = 3, /* the scratch allocation failed */
+  MS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  MS_ERR_TIMEOUT = 5        /* a device-side bounded wait expired */
+} ms_status;
+
+/* Bucket identifiers (Section 6 "Bucket identification", Section 7.1, 7.3). */
+typedef enum {
+  /* range splitters (Section 7.3 "Range histogram"): `splitters` holds m-1
+   * nondecreasing uint32 values s_1..s_{m-1} in DEVICE memory; the bucket of u
+   * is the number of splitters <= u (u < s_1 -> 0, u >= s_{m-1} -> m-1). */
+  MS_BUCKET_RANGE_U32 = 0,
+  /* delta buckets on float32 keys (Section 6, Section 7.3 "Even histogram"):
+   * q = (x - x0) / delta rounded to nearest in binary32, b = floor(q), then
+   * b <= 0 -> 0, b >= m (and +inf, NaN) -> m-1. */
+  MS_BUCKET_DELTA_F32 = 1,
+  /* radix digit (Section 7.1): (u >> shift) & (2^bits - 1); m must be 2^bits,
+   * 0 <= bits <= 8, shift + bits <= 32. */
+  MS_BUCKET_RADIX = 2,
+  /* u mod m. */
+  MS_BUCKET_MOD = 3
+} ms_bucket_kind;
+
+typedef struct {
+  int32_t kind;               /* an ms_bucket_kind */
+  uint32_t m;                 /* number of buckets, 1 <= m <= 256 */
+  const uint32_t *splitters;  /* RANGE_U32 only: device pointer, m-1 entries */
+  float x0, delta;            /* DELTA_F32 only: delta > 0 and finite */
+  uint32_t shift, bits;       /* RADIX only */
+} ms_bucket_spec;
+
+/* Stable multisplit of keys (Section 3.1, Eq. 1).
+ *   keys_in[n]   -> keys_out[n]: the keys grouped by bucket, buckets ascending,
+ *                   input order kept inside each bucket.
+ *   offsets[m+1] -> offsets[j] = start of bucket j in keys_out, offsets[m] = n
+ *                   (the paper's optional "beginning index of each bucket",
+ *                   with one extra entry).  May be NULL if not wanted.
+ * Errors: MS_ERR_INVALID_ARG for a NULL data pointer with n > 0, keys_in ==
+ * keys_out, n >= 2^32 or a bad spec (see ms_bucket_spec). */
+ms_status ms_multisplit_keys(const uint32_t *keys_in, size_t n, const ms_bucket_spec *spec,
+                             uint32_t *keys_out, uint32_t *offsets, void *stream);
+
+/* Stable multisplit of key-value pairs (Section 3.1; values are opaque 32-bit
+ * words carried along the same permutation as their keys). */
+ms_status ms_multisplit_pairs(const uint32_t *keys_in, const uint32_t *vals_in, size_t n,
+                              const ms_bucket_spec *spec, uint32_t *keys_out, uint32_t *vals_out,
+                              uint32_t *offsets, void *stream);
+
+/* LSD radix sort built on multisplit (Section 7.1): a stable sort of the keys
+ * (and values) by the key bits [begin_bit, end_bit), 0 <= begin_bit <=
+ * end_bit <= 32, in passes of 8-bit digits (the last pass takes the bits
+ * left over).  vals_in / vals_out may both be NULL (keys only).  keys_out /
+ * vals_out must not overlap the inputs.  The library holds one ping-pong
+ * buffer of n words (per array) in its pool during the call. */
+ms_status ms_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, size_t n, int begin_bit,
+                        int end_bit, uint32_t *keys_out, uint32_t *vals_out, void *stream);
+
+/* Reads and clears the calling device's status word: MS_OK, or
+ * MS_ERR_TIMEOUT if any bounded device-side wait expired since the last read.
+ * Synchronizes `stream` first. */
+ms_status ms_device_status(void *stream);
+
+/* Stage timing, a tracing aid in the spirit of the paper's per-stage timing
+ * (Table 4: pre-scan, scan, post-scan).  ms_stage_timing(1) clears the record
+ * and starts recording CUDA events on the launching stream around the three
+ * kernels of every multisplit (including each radix-sort pass) issued
+ * afterwards by this process; ms_stage_timing(0) stops recording (the record
+ * is kept).  ms_stage_times() waits for the recorded events and returns the
+ * summed milliseconds per stage and the number of recorded multisplits; any
+ * output pointer may be NULL.  Recording adds one event per stage boundary;
+ * clearing while another thread is inside a multisplit call is not supported.
+ * Returns MS_ERR_CUDA if an event query fails. */
+ms_status ms_stage_timing(int enable);
+ms_status ms_stage_times(double *prescan_ms, double *scan_ms, double *postscan_ms, uint64_t *multisplits);
+
+/* Human-readable name of a status code (static storage). */
+const char *ms_status_string(ms_status s);
+
+/* Library version string (static storage). */
+const char *ms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MS_H_ */

@@ -1,0 +1,237 @@
+"""ctypes binding of libms.so (include/ms.h): argument marshalling only.
+
+The functions named like the C entry points (``ms_multisplit_keys`` ...) take
+raw device pointers (ints), sizes and a stream handle exactly like the C ABI.
+The helpers below them (``multisplit_keys`` ...) take torch CUDA tensors,
+allocate the outputs with torch and call the C entry point on the current
+torch stream.  Every step of the computation runs in libms.so's CUDA kernels;
+there is no CPU path.  A missing or unloadable library raises ``MsError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libms.so")
+
+MS_OK, MS_ERR_INVALID_ARG, MS_ERR_UNSUPPORTED, MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA, MS_ERR_TIMEOUT = range(6)
+RANGE_U32, DELTA_F32, RADIX, MOD = 0, 1, 2, 3
+MAX_M = 256
+
+
+class MsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = _STATUS_NAMES.get(status, f"status {status}")
+        super().__init__(f"{what}: {name}" if what else name)
+
+
+_STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_INVALID_ARG", 2: "MS_ERR_UNSUPPORTED", 3: "MS_ERR_OUT_OF_MEMORY",
+                 4: "MS_ERR_CUDA", 5: "MS_ERR_TIMEOUT"}
+
+
+class _Spec(ctypes.Structure):
+    """ms_bucket_spec."""
+
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("m", ctypes.c_uint32),
+        ("splitters", ctypes.c_void_p),
+        ("x0", ctypes.c_float),
+        ("delta", ctypes.c_float),
+        ("shift", ctypes.c_uint32),
+        ("bits", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libms.so (built by ``paper_1701_01189_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MsError(MS_ERR_UNSUPPORTED, f"{LIB_PATH} is missing; run paper_1701_01189_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, S, I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        SP = ctypes.POINTER(_Spec)
+        L.ms_multisplit_keys.argtypes = [P, S, SP, P, P, P]
+        L.ms_multisplit_pairs.argtypes = [P, P, S, SP, P, P, P, P]
+        L.ms_radix_sort.argtypes = [P, P, S, I, I, P, P, P]
+        L.ms_device_status.argtypes = [P]
+        L.ms_status_string.argtypes = [I]
+        L.ms_status_string.restype = ctypes.c_char_p
+        L.ms_version.argtypes = []
+        L.ms_version.restype = ctypes.c_char_p
+        L.ms_stage_timing.argtypes = [I]
+        L.ms_stage_times.argtypes = [P, P, P, P]
+        for f in ("ms_multisplit_keys", "ms_multisplit_pairs", "ms_radix_sort", "ms_device_status",
+                  "ms_stage_timing", "ms_stage_times"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------- raw C entry points
+def ms_multisplit_keys(keys_in: int, n: int, spec: "_Spec", keys_out: int, offsets: int, stream: int) -> int:
+    return lib().ms_multisplit_keys(keys_in, n, ctypes.byref(spec), keys_out, offsets, stream)
+
+
+def ms_multisplit_pairs(keys_in: int, vals_in: int, n: int, spec: "_Spec", keys_out: int, vals_out: int,
+                        offsets: int, stream: int) -> int:
+    return lib().ms_multisplit_pairs(keys_in, vals_in, n, ctypes.byref(spec), keys_out, vals_out, offsets, stream)
+
+
+def ms_radix_sort(keys_in: int, vals_in: int, n: int, begin_bit: int, end_bit: int, keys_out: int,
+                  vals_out: int, stream: int) -> int:
+    return lib().ms_radix_sort(keys_in, vals_in, n, begin_bit, end_bit, keys_out, vals_out, stream)
+
+
+def ms_device_status(stream: int) -> int:
+    return lib().ms_device_status(stream)
+
+
+def ms_stage_timing(enable: int) -> int:
+    return lib().ms_stage_timing(int(enable))
+
+
+def ms_stage_times():
+    """(prescan_ms, scan_ms, postscan_ms, multisplits) recorded since ms_stage_timing(1)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    k = ctypes.c_uint64()
+    _check(lib().ms_stage_times(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(k)),
+           "ms_stage_times")
+    return a.value, b.value, c.value, k.value
+
+
+def ms_status_string(status: int) -> str:
+    return lib().ms_status_string(status).decode()
+
+
+def ms_version() -> str:
+    return lib().ms_version().decode()
+
+
+# ----------------------------------------------------------------- torch-tensor helpers
+@dataclass
+class BucketSpec:
+    """A bucket identifier (Section 6, 7.1, 7.3); mirrors ms_bucket_spec.
+
+    For RANGE_U32, ``splitters`` is a torch uint32/int32 CUDA tensor of m-1
+    nondecreasing values (kept alive by this object).
+    """
+
+    kind: int
+    m: int
+    splitters: Optional[object] = None
+    x0: float = 0.0
+    delta: float = 1.0
+    shift: int = 0
+    bits: int = 0
+
+    def c(self) -> _Spec:
+        ptr = None
+        if self.splitters is not None:
+            ptr = self.splitters.data_ptr()
+        return _Spec(self.kind, self.m, ptr, self.x0, self.delta, self.shift, self.bits)
+
+    @staticmethod
+    def range_u32(splitters) -> "BucketSpec":
+        return BucketSpec(RANGE_U32, int(splitters.numel()) + 1, splitters=splitters)
+
+    @staticmethod
+    def delta_f32(m: int, delta: float, x0: float = 0.0) -> "BucketSpec":
+        return BucketSpec(DELTA_F32, m, x0=x0, delta=delta)
+
+    @staticmethod
+    def radix(shift: int, bits: int) -> "BucketSpec":
+        return BucketSpec(RADIX, 1 << bits, shift=shift, bits=bits)
+
+    @staticmethod
+    def mod(m: int) -> "BucketSpec":
+        return BucketSpec(MOD, m)
+
+
+def _check(status: int, what: str):
+    if status != MS_OK:
+        raise MsError(status, what)
+
+
+def _stream(stream) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _u32_view(t):
+    import torch
+
+    if not t.is_cuda:
+        raise MsError(MS_ERR_INVALID_ARG, "tensor must live on a CUDA device")
+    if t.dtype not in (torch.int32, torch.uint32, torch.float32):
+        raise MsError(MS_ERR_INVALID_ARG, "tensor must hold 32-bit elements")
+    if not t.is_contiguous():
+        raise MsError(MS_ERR_INVALID_ARG, "tensor must be contiguous")
+    return t
+
+
+def multisplit_keys(keys, spec: BucketSpec, keys_out=None, offsets=None, stream=None):
+    """Stable multisplit of a 1-D CUDA tensor of 32-bit keys.  Returns (keys_out, offsets[m+1])."""
+    import torch
+
+    keys = _u32_view(keys)
+    n = keys.numel()
+    if keys_out is None:
+        keys_out = torch.empty_like(keys)
+    if offsets is None:
+        offsets = torch.empty(spec.m + 1, dtype=torch.int32, device=keys.device)
+    cs = spec.c()
+    _check(ms_multisplit_keys(keys.data_ptr(), n, cs, keys_out.data_ptr(), offsets.data_ptr(), _stream(stream)),
+           "ms_multisplit_keys")
+    return keys_out, offsets
+
+
+def multisplit_pairs(keys, vals, spec: BucketSpec, keys_out=None, vals_out=None, offsets=None, stream=None):
+    """Stable multisplit of (key, value) pairs.  Returns (keys_out, vals_out, offsets[m+1])."""
+    import torch
+
+    keys, vals = _u32_view(keys), _u32_view(vals)
+    n = keys.numel()
+    if vals.numel() != n:
+        raise MsError(MS_ERR_INVALID_ARG, "keys and values differ in length")
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    vals_out = torch.empty_like(vals) if vals_out is None else vals_out
+    if offsets is None:
+        offsets = torch.empty(spec.m + 1, dtype=torch.int32, device=keys.device)
+    cs = spec.c()
+    _check(ms_multisplit_pairs(keys.data_ptr(), vals.data_ptr(), n, cs, keys_out.data_ptr(), vals_out.data_ptr(),
+                               offsets.data_ptr(), _stream(stream)), "ms_multisplit_pairs")
+    return keys_out, vals_out, offsets
+
+
+def radix_sort(keys, vals=None, begin_bit: int = 0, end_bit: int = 32, keys_out=None, vals_out=None,
+               stream=None):
+    """LSD multisplit radix sort (Section 7.1).  Returns (keys_out, vals_out or None)."""
+    import torch
+
+    keys = _u32_view(keys)
+    n = keys.numel()
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    vptr = voptr = None
+    if vals is not None:
+        vals = _u32_view(vals)
+        vals_out = torch.empty_like(vals) if vals_out is None else vals_out
+        vptr, voptr = vals.data_ptr(), vals_out.data_ptr()
+    _check(ms_radix_sort(keys.data_ptr(), vptr, n, begin_bit, end_bit, keys_out.data_ptr(), voptr,
+                         _stream(stream)), "ms_radix_sort")
+    return keys_out, (vals_out if vals is not None else None)
+
+
+def device_status(stream=None) -> int:
+    """MS_OK, or MS_ERR_TIMEOUT if a device-side bounded wait expired (clears it)."""
+    return ms_device_status(_stream(stream))

@@ -1,0 +1,58 @@
+// ms_host.h -- host-side internals shared by the C ABI and the per-kind
+// launcher translation units (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ms_device.cuh"
+
+namespace ms {
+
+// Per-device state, created on the first call made with that device current.
+struct DeviceCtx {
+  int device = -1;
+  int sm_count = 0;
+  cudaMemPool_t pool = nullptr;  // library-owned stream-ordered pool for scratch
+  uint32_t* d_err = nullptr;     // device status word (MS_OK or MS_ERR_TIMEOUT)
+};
+
+// One multisplit request, validated, in kernel terms.
+struct Call {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;  // nullptr: keys only
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  uint32_t* offsets;        // nullptr: not wanted
+  uint32_t n;
+  int kind;
+  DevSpec sp;
+  cudaStream_t stream;
+};
+
+// Tile configuration: NW warps per CTA, ITEMS keys per lane per tile.
+struct TileCfg {
+  int nw;
+  int items;
+};
+
+// Runs the three stages for one request.  Defined per bucket kind in
+// ms_kind_<kind>.cu.
+cudaError_t run_multisplit_range(const Call& c, DeviceCtx& ctx);
+cudaError_t run_multisplit_delta(const Call& c, DeviceCtx& ctx);
+cudaError_t run_multisplit_radix(const Call& c, DeviceCtx& ctx);
+cudaError_t run_multisplit_mod(const Call& c, DeviceCtx& ctx);
+
+cudaError_t run_multisplit(const Call& c, DeviceCtx& ctx);
+
+// Stage timing (ms_trace.cu): trace_begin records the start event and returns
+// a slot (-1 when timing is off); trace_mark records event `stage` (1..3).
+int trace_begin(cudaStream_t s);
+void trace_mark(int slot, int stage, cudaStream_t s);
+
+// Scratch from the library pool, ordered on `stream`.
+cudaError_t scratch_alloc(DeviceCtx& ctx, void** p, size_t bytes, cudaStream_t stream);
+cudaError_t scratch_free(void* p, cudaStream_t stream);
+
+}  // namespace ms

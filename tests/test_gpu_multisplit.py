@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA multisplit (through the C ABI) against the CPU oracle,
+element by element, bit exact.  Sizes span several tiles and ragged tails;
+edge cases cover empty input, single elements, all keys in one bucket, sorted
+and reverse-sorted keys, every m from 1 to 256 for key mod m, duplicated
+splitters, float32 special values, and the full-size configurations."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from parity import Case, check_multisplit, range_case, run_gpu, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TILE = 4096  # tile of the default configuration (16 warps x 32 lanes x 8 keys)
+SIZES = [0, 1, 31, 32, 33, 255, 1000, TILE - 1, TILE, TILE + 1, 3 * TILE + 17, 65537, 1 << 20]
+MS = [1, 2, 3, 8, 31, 32, 33, 64, 255, 256]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import paper_1701_01189_gb300 as ms
+    from paper_1701_01189_gb300.build import build
+
+    build()
+    ms.lib()
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+@pytest.mark.parametrize("m", MS)
+def test_range_sizes(m, pairs):
+    for i, n in enumerate(SIZES):
+        keys = synthetic.uniform_u32(n, 1000 + i)
+        vals = synthetic.index_values(n) if pairs else None
+        check_multisplit(keys, vals, range_case(m, 7 + m))
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+@pytest.mark.parametrize("m", [2, 8, 32, 64, 256])
+def test_range_skewed(m, pairs):
+    spl = synthetic.range_splitters(m, 3)
+    n = 200_003
+    keys = synthetic.skewed_u32(n, spl, 4)
+    vals = synthetic.index_values(n) if pairs else None
+    check_multisplit(keys, vals, Case(oracle.RANGE_U32, m, splitters=spl))
+
+
+def test_range_duplicate_splitters_and_boundaries():
+    for m in (3, 9, 40, 256):
+        spl = synthetic.range_splitters(m, 5)
+        spl[1:m // 2] = spl[1]  # many empty buckets
+        keys = np.concatenate([spl, spl - np.uint32(1), spl + np.uint32(1), np.array([0, 0xFFFFFFFF], np.uint32),
+                               synthetic.uniform_u32(10000, 6)])
+        check_multisplit(keys, synthetic.index_values(len(keys)), Case(oracle.RANGE_U32, m, splitters=spl))
+
+
+@pytest.mark.parametrize("m", list(range(1, 257)))
+def test_mod_every_m(m):
+    n = 5000 + m
+    keys = np.concatenate([np.array([0, 1, m - 1, m, 0xFFFFFFFF, 0xFFFFFFFE, 0x80000000], np.uint32),
+                           synthetic.uniform_u32(n, m)])
+    check_multisplit(keys, synthetic.index_values(len(keys)), Case(oracle.MOD, m))
+
+
+@pytest.mark.parametrize("shift,bits", [(0, 0), (0, 1), (31, 1), (0, 4), (29, 3), (24, 8), (13, 8), (0, 8),
+                                        (27, 5), (26, 6)])
+def test_radix_digit(shift, bits):
+    for n in (TILE * 5 + 3, 100_000):
+        keys = synthetic.uniform_u32(n, shift * 10 + bits)
+        check_multisplit(keys, synthetic.index_values(n), Case(oracle.RADIX, 1 << bits, shift=shift, bits=bits))
+
+
+@pytest.mark.parametrize("m", [1, 2, 8, 32, 64, 256, 7, 100])
+def test_delta_f32(m):
+    delta = np.float32(1000.0) / np.float32(m)
+    grid = (np.arange(m + 1, dtype=np.float32) * delta).astype(np.float32)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, -5.0, 1e30, -1e30, 1e-45, 999.9999],
+                       np.float32)
+    near = np.concatenate([grid, np.nextafter(grid, np.float32(-np.inf)), np.nextafter(grid, np.float32(np.inf)),
+                           special]).astype(np.float32)
+    keys = np.concatenate([near.view(np.uint32), synthetic.uniform_f32_1000(70_000, m)])
+    check_multisplit(keys, synthetic.index_values(len(keys)), Case(oracle.DELTA_F32, m, x0=0.0, delta=float(delta)))
+    check_multisplit(keys, None, Case(oracle.DELTA_F32, m, x0=-3.5, delta=float(delta) * 0.75))
+
+
+@pytest.mark.parametrize("pattern", ["same", "sorted", "reversed", "one_bucket", "alternating"])
+@pytest.mark.parametrize("m", [2, 32, 256])
+def test_patterns(pattern, m):
+    n = 3 * TILE + 5
+    base = synthetic.uniform_u32(n, 99)
+    if pattern == "same":
+        keys = np.full(n, 0x12345678, np.uint32)
+    elif pattern == "sorted":
+        keys = np.sort(base)
+    elif pattern == "reversed":
+        keys = np.sort(base)[::-1].copy()
+    elif pattern == "one_bucket":
+        keys = (base % np.uint32(97)) * np.uint32(m)  # mod m == 0 for all
+    else:
+        keys = np.arange(n, dtype=np.uint32)
+    check_multisplit(keys, synthetic.index_values(n), Case(oracle.MOD, m))
+    check_multisplit(keys, None, range_case(m, 1))
+
+
+def test_offsets_null_and_empty():
+    import paper_1701_01189_gb300 as ms
+    import torch
+
+    keys = synthetic.uniform_u32(TILE + 3, 1)
+    dk = to_dev(keys)
+    out = torch.empty_like(dk)
+    spec = Case(oracle.MOD, 8).gpu_spec()
+    st = ms.ms_multisplit_keys(dk.data_ptr(), dk.numel(), spec.c(), out.data_ptr(), None,
+                               torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK
+    ok, _, _ = oracle.multisplit(keys, None, oracle.Spec(oracle.MOD, 8))
+    np.testing.assert_array_equal(to_host(out), ok)
+    # n = 0: offsets all zero, nothing else touched
+    off = torch.full((9,), 7, dtype=torch.int32, device="cuda")
+    st = ms.ms_multisplit_keys(0, 0, spec.c(), 0, off.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK
+    assert to_host(off).tolist() == [0] * 9
+
+
+def test_repeated_calls_and_streams():
+    """Same result on a side stream, twice in a row (scratch reused from the pool)."""
+    import paper_1701_01189_gb300 as ms
+    import torch
+
+    keys = synthetic.uniform_u32(300_000, 17)
+    vals = synthetic.index_values(300_000)
+    case = range_case(64, 2)
+    ok, ov, ooff = oracle.multisplit(keys, vals, case.oracle_spec())
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dk, dv = to_dev(keys), to_dev(vals)
+        for _ in range(2):
+            ko, vo, off = ms.multisplit_pairs(dk, dv, case.gpu_spec(), stream=s)
+            s.synchronize()
+            np.testing.assert_array_equal(to_host(ko), ok)
+            np.testing.assert_array_equal(to_host(vo), ov)
+
+
+# ----------------------------------------------------------------- full-size configurations
+def test_config_plain_2p20_key_shift29():
+    """n = 2^20 uniform keys, m = 8, bucket = key >> 29, keys only, 9 offsets."""
+    keys = synthetic.uniform_u32(1 << 20, 1)
+    gk, _, goff = run_gpu(keys, None, Case(oracle.RADIX, 8, shift=29, bits=3))
+    ok, _, ooff = oracle.multisplit(keys, None, oracle.Spec(oracle.RADIX, 8, shift=29, bits=3))
+    assert len(goff) == 9
+    np.testing.assert_array_equal(goff.astype(np.uint64), ooff)
+    np.testing.assert_array_equal(gk, ok)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "skewed"])
+@pytest.mark.parametrize("m", [2, 8, 32, 64, 256])
+def test_config_sweep_2p26(m, dist):
+    """n = 2^26 range buckets, keys only and key-value (value = index)."""
+    n = 1 << 26
+    spl = synthetic.range_splitters(m, 1000 + m)
+    keys = synthetic.uniform_u32(n, 2000 + m) if dist == "uniform" else synthetic.skewed_u32(n, spl, 3000 + m)
+    case = Case(oracle.RANGE_U32, m, splitters=spl)
+    check_multisplit(keys, None, case)
+    check_multisplit(keys, synthetic.index_values(n), case)
+
+
+@pytest.mark.parametrize("m", [2, 8, 32, 64, 256])
+def test_config_sweep_2p26_f32(m):
+    n = 1 << 26
+    keys = synthetic.uniform_f32_1000(n, 4000 + m)
+    case = Case(oracle.DELTA_F32, m, x0=0.0, delta=float(np.float32(1000.0) / np.float32(m)))
+    check_multisplit(keys, None, case)
+    check_multisplit(keys, synthetic.index_values(n), case)
