@@ -117,6 +117,14 @@ ms_status ms_device_status(void *stream);
 ms_status ms_stage_timing(int enable);
 ms_status ms_stage_times(double *prescan_ms, double *scan_ms, double *postscan_ms, uint64_t *multisplits);
 
+/* Failure-path test aid.  Runs the look-back scan kernel as the second of two
+ * scan tiles while the first tile's status word is never published, so its
+ * bounded wait must run out (after about one second).  The kernel then records
+ * MS_ERR_TIMEOUT in the device status word and returns; it touches only
+ * library scratch.  Returns MS_OK when the launch was enqueued; the caller then
+ * reads ms_device_status(), which must report MS_ERR_TIMEOUT. */
+ms_status ms_test_expire_lookback(void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *ms_status_string(ms_status s);
 

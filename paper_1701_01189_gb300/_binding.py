@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
         L.ms_status_string.restype = ctypes.c_char_p
         L.ms_version.argtypes = []
         L.ms_version.restype = ctypes.c_char_p
+        L.ms_test_expire_lookback.argtypes = [P]
+        L.ms_test_expire_lookback.restype = ctypes.c_int
         L.ms_stage_timing.argtypes = [I]
         L.ms_stage_times.argtypes = [P, P, P, P]
         for f in ("ms_multisplit_keys", "ms_multisplit_pairs", "ms_radix_sort", "ms_device_status",
@@ -93,6 +95,10 @@ def ms_radix_sort(keys_in: int, vals_in: int, n: int, begin_bit: int, end_bit: i
 
 def ms_device_status(stream: int) -> int:
     return lib().ms_device_status(stream)
+
+
+def ms_test_expire_lookback(stream: int) -> int:
+    return lib().ms_test_expire_lookback(stream)
 
 
 def ms_stage_timing(enable: int) -> int:

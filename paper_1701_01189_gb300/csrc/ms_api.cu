@@ -7,6 +7,7 @@
 
 #include "ms.h"
 #include "ms_host.h"
+#include "ms_scan.cuh"
 
 namespace ms {
 
@@ -249,6 +250,30 @@ extern "C" ms_status ms_radix_sort(const uint32_t* keys_in, const uint32_t* vals
     src_v = dst_v;
   }
   const cudaError_t e2 = scratch_free(tmp, s);
+  return to_status(e != cudaSuccess ? e : e2);
+}
+
+extern "C" ms_status ms_test_expire_lookback(void* stream) {
+  DeviceCtx* ctx = nullptr;
+  ms_status st = current_ctx(&ctx);
+  if (st != MS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // scratch: two scan tiles of data | two status words | ticket
+  const size_t data_bytes = (size_t)2 * kScanTile * 4;
+  void* ws = nullptr;
+  cudaError_t e = scratch_alloc(*ctx, &ws, data_bytes + 16 + 16, s);
+  if (e != cudaSuccess) return to_status(e);
+  auto* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + data_bytes);
+  auto* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + data_bytes + 16);
+  e = cudaMemsetAsync(ws, 0, data_bytes + 16, s);
+  const uint32_t one = 1;  // the only CTA takes ticket 1: its predecessor never runs
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ticket, &one, sizeof one, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // `one` lives on this stack frame
+  if (e == cudaSuccess) {
+    ScanArgs a{static_cast<uint32_t*>(ws), (uint32_t)(2 * kScanTile), 1u, nullptr, 1u, status, ticket, ctx->d_err};
+    e = launch_scan_tiles(a, 1, s);
+  }
+  const cudaError_t e2 = scratch_free(ws, s);
   return to_status(e != cudaSuccess ? e : e2);
 }
 

@@ -58,4 +58,9 @@ cudaError_t launch_scan_lookback(const ScanArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan_tiles(const ScanArgs& a, uint32_t ctas, cudaStream_t stream) {
+  k_scan_lookback<<<ctas, kScanThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace ms

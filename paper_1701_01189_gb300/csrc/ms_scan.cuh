@@ -55,4 +55,7 @@ __device__ __forceinline__ unsigned long long wait_status(const unsigned long lo
 // words and the ticket must be zero.  Defined in ms_scan.cu.
 cudaError_t launch_scan_lookback(const ScanArgs& a, cudaStream_t stream);
 
+// Launches exactly `ctas` CTAs of the same kernel (failure-path test aid).
+cudaError_t launch_scan_tiles(const ScanArgs& a, uint32_t ctas, cudaStream_t stream);
+
 }  // namespace ms

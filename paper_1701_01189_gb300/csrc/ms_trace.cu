@@ -47,8 +47,10 @@ using namespace ms;
 
 extern "C" ms_status ms_stage_timing(int enable) {
   std::lock_guard<std::mutex> lock(g_mu);
-  for (auto& q : g_used) g_free.push_back(q);
-  g_used.clear();
+  if (enable) {
+    for (auto& q : g_used) g_free.push_back(q);
+    g_used.clear();
+  }
   g_on = enable != 0;
   return MS_OK;
 }
