@@ -87,6 +87,8 @@ static ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kin
   std::memset(&d, 0, sizeof d);
   d.m = m;
   d.nbits = ceil_log2(m);
+  d.m_pad = m <= 32 ? 32u : ((m + 31u) & ~31u);
+  d.lut_bits = m <= 64 ? 10u : 11u;
   switch (spec->kind) {
     case MS_BUCKET_RANGE_U32:
       if (m > 1 && spec->splitters == nullptr) return MS_ERR_INVALID_ARG;
@@ -236,6 +238,8 @@ extern "C" ms_status ms_radix_sort(const uint32_t* keys_in, const uint32_t* vals
     c.kind = kRadix;
     c.sp.m = 1u << bits;
     c.sp.nbits = (uint32_t)bits;
+    c.sp.m_pad = c.sp.m <= 32 ? 32u : c.sp.m;
+    c.sp.lut_bits = 10u;
     c.sp.shift = (uint32_t)shift;
     c.sp.mask = (1u << bits) - 1u;
     c.keys_in = src_k;

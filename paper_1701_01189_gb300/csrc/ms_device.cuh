@@ -35,6 +35,8 @@ struct DevSpec {
   float x0, delta;            // kDelta
   uint32_t shift, mask;       // kRadix: shift < 32
   uint32_t mod_magic, mod_sh1, mod_sh2;  // kMod: multiply-shift constants
+  uint32_t m_pad;             // m rounded up to a multiple of 32 (at least 32)
+  uint32_t lut_bits;          // kRange: key bits indexing the splitter lookup table
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -44,77 +46,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
-
-// Range splitters go to shared memory as a table of 2^nbits - 1 entries
-// padded with 0xffffffff, so the search below needs no bounds test.
-__device__ __forceinline__ void load_splitter_table(const DevSpec& sp, uint32_t* tbl) {
-  const uint32_t P = 1u << sp.nbits;
-  for (uint32_t i = threadIdx.x; i + 1 < P; i += blockDim.x)
-    tbl[i] = (i + 1 < sp.m) ? sp.splitters[i] : 0xffffffffu;
-}
-
-// f(u) for the bucket kind KIND.
-template <int KIND>
-__device__ __forceinline__ uint32_t bucket_of(uint32_t u, const DevSpec& sp, const uint32_t* tbl) {
-  if constexpr (KIND == kRange) {
-    // number of table entries <= u, by halving steps over a table of
-    // 2^nbits - 1 sorted entries; the padding only counts when u is
-    // 0xffffffff, and the clamp to m-1 absorbs it.
-    uint32_t pos = 0;
-    for (uint32_t h = (1u << sp.nbits) >> 1; h > 0; h >>= 1) pos += (tbl[pos + h - 1] <= u) ? h : 0u;
-    return min(pos, sp.m - 1);
-  } else if constexpr (KIND == kDelta) {
-    const float x = __uint_as_float(u);
-    const float q = __fdiv_rn(__fsub_rn(x, sp.x0), sp.delta);  // IEEE round-to-nearest
-    const float f = floorf(q);
-    if (!(f < (float)sp.m)) return sp.m - 1;  // f >= m, +inf, NaN
-    if (f <= 0.0f) return 0u;                 // negative, -0, -inf
-    return (uint32_t)f;
-  } else if constexpr (KIND == kRadix) {
-    return (u >> sp.shift) & sp.mask;
-  } else {
-    // u mod m by the multiply-shift division of Granlund and Montgomery
-    // ("Division by invariant integers using multiplication", PLDI 1994,
-    // unsigned case): q = (t + ((u - t) >> sh1)) >> sh2 with t = mulhi(M, u).
-    const uint32_t t = __umulhi(sp.mod_magic, u);
-    const uint32_t q = (t + ((u - t) >> sp.mod_sh1)) >> sp.mod_sh2;
-    return u - q * sp.m;
-  }
-}
-
-// Ballot-based voting of one 32-key window (Section 5.4): after the loop,
-// `own` holds the valid lanes whose bucket equals this lane's bucket b, and
-// `lane_bm` the valid lanes whose bucket equals this lane's id (Alg. 2; only
-// meaningful for lane ids < m <= 32).
-template <int MAXBITS>
-__device__ __forceinline__ void window_vote(uint32_t b, bool valid, uint32_t nbits, uint32_t& own,
-                                            uint32_t& lane_bm) {
-  const uint32_t vb = __ballot_sync(kFull, valid);
-  const uint32_t lane = lane_id();
-  own = vb;
-  lane_bm = vb;
-#pragma unroll
-  for (int k = 0; k < MAXBITS; ++k) {
-    if (k < (int)nbits) {
-      const uint32_t bal = __ballot_sync(kFull, (b >> k) & 1u);
-      own &= ((b >> k) & 1u) ? bal : ~bal;
-      lane_bm &= ((lane >> k) & 1u) ? bal : ~bal;
-    }
-  }
-}
-
-// Same voting, `own` only (buckets up to 256: eight ballots).
-__device__ __forceinline__ uint32_t window_peers(uint32_t b, bool valid, uint32_t nbits) {
-  uint32_t own = __ballot_sync(kFull, valid);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (k < (int)nbits) {
-      const uint32_t bal = __ballot_sync(kFull, (b >> k) & 1u);
-      own &= ((b >> k) & 1u) ? bal : ~bal;
-    }
-  }
-  return own;
-}
 
 // Exclusive prefix sum over the first `count` threads of the block (count <=
 // 32 * number of warps); every thread passes v (0 beyond count).  Returns the

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include "ms_host.h"
@@ -13,25 +14,29 @@
 namespace ms {
 
 // Per-device, per-instantiation launch set-up: the dynamic shared memory
-// opt-in and the number of CTAs resident per SM.
+// opt-in (once, for the largest size the instantiation can use) and the
+// number of CTAs resident per SM for each shared-memory size seen.
 struct LaunchInfo {
   std::mutex mu;
-  uint64_t ready = 0;  // bit d: set up on device d
-  int resident[64] = {};
+  uint64_t ready = 0;  // bit d: opt-in done on device d
+  std::map<std::pair<int, size_t>, int> resident;
 };
 
 template <typename K>
-static int setup_kernel(LaunchInfo& li, K kernel, int threads, size_t smem, int device) {
+static int setup_kernel(LaunchInfo& li, K kernel, int threads, size_t smem_max, size_t smem, int device) {
   std::lock_guard<std::mutex> lock(li.mu);
   const int d = device & 63;
   if (!((li.ready >> d) & 1ull)) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess || v < 1) v = 1;
-    li.resident[d] = v;
+    if (smem_max > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     li.ready |= 1ull << d;
   }
-  return li.resident[d];
+  auto key = std::make_pair(d, smem);
+  auto it = li.resident.find(key);
+  if (it != li.resident.end()) return it->second;
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess || v < 1) v = 1;
+  li.resident[key] = v;
+  return v;
 }
 
 // Chunking of L tiles over at most `max_ctas` CTAs: K tiles per chunk, G chunks.
@@ -47,20 +52,26 @@ static inline Chunking make_chunking(uint32_t n, uint32_t T, uint32_t max_ctas) 
   return ch;
 }
 
-template <int KIND, int NW, int ITEMS, bool SMALLM, bool PAIRS>
+template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK>
 static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   constexpr int THREADS = NW * 32;
   constexpr uint32_t T = THREADS * ITEMS;
-  static_assert(NW >= 8, "the per-bucket block phase needs >= 256 threads");
-  auto kpre = k_prescan<KIND, NW, ITEMS, SMALLM>;
-  auto kpost = k_postscan<KIND, NW, ITEMS, SMALLM, PAIRS>;
-  const size_t smem_pre = prescan_smem_bytes<NW, SMALLM>();
-  const size_t smem_post = postscan_smem_bytes<NW, ITEMS, SMALLM, PAIRS>();
+  auto kpre = k_prescan<KIND, NB, NW, ITEMS>;
+  auto kpost = k_postscan<KIND, NB, NW, ITEMS, PAIRS, RANK>;
+  const uint32_t m_pad = c.sp.m_pad, lb = c.sp.lut_bits;
+  // shared memory is sized for the largest m of this instantiation so the
+  // occupancy query is made once
+  const uint32_t mp_max = (KIND == kRadix || RANK == kRankBallot) ? (NB <= 5 ? 32u : (1u << NB)) : 256u;
+  const size_t smem_pre_max = prescan_smem_bytes<KIND, NW>(mp_max, 11);
+  const size_t smem_post_max = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK>(mp_max, 11);
+  const size_t smem_pre = prescan_smem_bytes<KIND, NW>(m_pad, lb);
+  const size_t smem_post = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK>(m_pad, lb);
   static LaunchInfo li_pre, li_post;
-  const int nb_post = setup_kernel(li_post, kpost, THREADS, smem_post, ctx.device);
-  setup_kernel(li_pre, kpre, THREADS, smem_pre, ctx.device);
+  const int nb_post = setup_kernel(li_post, kpost, THREADS, smem_post_max, smem_post, ctx.device);
+  const int nb_pre = setup_kernel(li_pre, kpre, THREADS, smem_pre_max, smem_pre, ctx.device);
 
-  const Chunking ch = make_chunking(c.n, T, (uint32_t)(ctx.sm_count * nb_post));
+  const int resident = nb_post < nb_pre ? nb_post : nb_pre;
+  const Chunking ch = make_chunking(c.n, T, (uint32_t)(ctx.sm_count * resident));
   const uint32_t m = c.sp.m;
   const uint32_t len = m * ch.G;
   const uint32_t nscan = (len + kScanTile - 1) / kScanTile;
@@ -77,9 +88,10 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   auto* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes);
   e = cudaMemsetAsync(status, 0, st_bytes + 16, c.stream);
 
+  const uint32_t aligned = ((reinterpret_cast<uintptr_t>(c.keys_in) | reinterpret_cast<uintptr_t>(c.vals_in)) & 15u) == 0;
   const int slot = trace_begin(c.stream);
   if (e == cudaSuccess) {
-    PrescanArgs pa{c.keys_in, c.n, c.sp, ch.K, ch.L, ch.G, H};
+    PrescanArgs pa{c.keys_in, c.n, c.sp, ch.K, ch.L, ch.G, H, aligned};
     kpre<<<ch.G, THREADS, smem_pre, c.stream>>>(pa);
     e = cudaGetLastError();
     trace_mark(slot, 1, c.stream);
@@ -90,7 +102,8 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
     trace_mark(slot, 2, c.stream);
   }
   if (e == cudaSuccess) {
-    PostscanArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, c.sp, ch.K, ch.L, ch.G, H, ctx.d_err};
+    PostscanArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, c.sp, ch.K, ch.L, ch.G, H, ctx.d_err,
+                    aligned, 1u};
     kpost<<<ch.G, THREADS, smem_post, c.stream>>>(qa);
     e = cudaGetLastError();
     trace_mark(slot, 3, c.stream);
@@ -99,14 +112,31 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   return e != cudaSuccess ? e : e2;
 }
 
+// Tile: 8 warps x 32 lanes x 16 keys = 4096 keys.  Ranks by ballots for m <= 4
+// (one or two ballots per window), by the peer table otherwise.
+template <int KIND, int NB>
+static cudaError_t run_ms_nb(const Call& c, DeviceCtx& ctx) {
+  constexpr int RANK = NB <= 2 ? kRankBallot : kRankTable;
+  // identifiers other than range splitters do not depend on NB in table mode:
+  // share one instantiation
+  constexpr int NBK = (KIND == kRange || RANK == kRankBallot) ? NB : 8;
+  if (c.vals_in != nullptr) return run_ms_cfg<KIND, NBK, 8, 16, true, RANK>(c, ctx);
+  return run_ms_cfg<KIND, NBK, 8, 16, false, RANK>(c, ctx);
+}
+
 template <int KIND>
 static cudaError_t run_ms_kind(const Call& c, DeviceCtx& ctx) {
-  const bool pairs = c.vals_in != nullptr;
-  const bool smallm = c.sp.m <= 32;
-  if (smallm) {
-    return pairs ? run_ms_cfg<KIND, 16, 8, true, true>(c, ctx) : run_ms_cfg<KIND, 16, 8, true, false>(c, ctx);
+  switch (c.sp.nbits) {
+    case 0: return run_ms_nb<KIND, 0>(c, ctx);
+    case 1: return run_ms_nb<KIND, 1>(c, ctx);
+    case 2: return run_ms_nb<KIND, 2>(c, ctx);
+    case 3: return run_ms_nb<KIND, 3>(c, ctx);
+    case 4: return run_ms_nb<KIND, 4>(c, ctx);
+    case 5: return run_ms_nb<KIND, 5>(c, ctx);
+    case 6: return run_ms_nb<KIND, 6>(c, ctx);
+    case 7: return run_ms_nb<KIND, 7>(c, ctx);
+    default: return run_ms_nb<KIND, 8>(c, ctx);
   }
-  return pairs ? run_ms_cfg<KIND, 16, 8, false, true>(c, ctx) : run_ms_cfg<KIND, 16, 8, false, false>(c, ctx);
 }
 
 }  // namespace ms
