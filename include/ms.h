@@ -125,6 +125,22 @@ ms_status ms_stage_times(double *prescan_ms, double *scan_ms, double *postscan_m
  * reads ms_device_status(), which must report MS_ERR_TIMEOUT. */
 ms_status ms_test_expire_lookback(void *stream);
 
+/* Kernel-variant tuning (not in the paper, which fixed its parameters per
+ * architecture by hand, Section 6 "Parameters").  Every multisplit looks up
+ * its variant by (bucket kind, pairs 0/1, ceil(log2 m) in 0..8, size class of
+ * n from ms_tune_size_class: 0 below 2^16, 1 below 2^20, 2 below 2^24, 3
+ * otherwise).  A variant is: shape of the post-scan tile (0: 8 warps x 16
+ * keys per lane, 1: 16 x 8, 2: 8 x 8), rank mode (0: warp ballots, allowed
+ * for ceil(log2 m) <= 3; 1: per-warp peer tables) and reorder (1: reorder each
+ * tile in shared memory before writing, 0: write from registers; 0 requires
+ * rank mode 0).  Unset entries use built-in defaults.  The tuner in
+ * paper_1701_01189_gb300/autotune.py measures the candidates and sets the
+ * fastest.  MS_ERR_INVALID_ARG for out-of-range arguments. */
+int ms_tune_size_class(size_t n);
+ms_status ms_tune_set(int kind, int pairs, int log2m, int size_class, int shape, int rank, int reorder);
+ms_status ms_tune_get(int kind, int pairs, int log2m, int size_class, int *shape, int *rank, int *reorder);
+ms_status ms_tune_reset(void);
+
 /* Human-readable name of a status code (static storage). */
 const char *ms_status_string(ms_status s);
 

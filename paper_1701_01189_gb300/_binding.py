@@ -67,6 +67,13 @@ def lib() -> ctypes.CDLL:
         L.ms_status_string.restype = ctypes.c_char_p
         L.ms_version.argtypes = []
         L.ms_version.restype = ctypes.c_char_p
+        L.ms_tune_size_class.argtypes = [S]
+        L.ms_tune_size_class.restype = ctypes.c_int
+        L.ms_tune_set.argtypes = [I, I, I, I, I, I, I]
+        L.ms_tune_get.argtypes = [I, I, I, I, P, P, P]
+        L.ms_tune_reset.argtypes = []
+        for f in ("ms_tune_set", "ms_tune_get", "ms_tune_reset"):
+            getattr(L, f).restype = ctypes.c_int
         L.ms_test_expire_lookback.argtypes = [P]
         L.ms_test_expire_lookback.restype = ctypes.c_int
         L.ms_stage_timing.argtypes = [I]
@@ -112,6 +119,26 @@ def ms_stage_times():
     _check(lib().ms_stage_times(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(k)),
            "ms_stage_times")
     return a.value, b.value, c.value, k.value
+
+
+def ms_tune_size_class(n: int) -> int:
+    return lib().ms_tune_size_class(n)
+
+
+def ms_tune_set(kind: int, pairs: int, log2m: int, size_class: int, shape: int, rank: int, reorder: int) -> int:
+    return lib().ms_tune_set(kind, pairs, log2m, size_class, shape, rank, reorder)
+
+
+def ms_tune_get(kind: int, pairs: int, log2m: int, size_class: int):
+    """(shape, rank, reorder) used for that key."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().ms_tune_get(kind, pairs, log2m, size_class, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "ms_tune_get")
+    return a.value, b.value, c.value
+
+
+def ms_tune_reset() -> int:
+    return lib().ms_tune_reset()
 
 
 def ms_status_string(status: int) -> str:

@@ -1,0 +1,99 @@
+"""Autotuner for the multisplit kernel variants.
+
+For a set of workloads (bucket kind, m, keys or pairs, n) it times every
+variant the library offers -- post-scan tile shape (8 warps x 16 keys, 16 x 8,
+8 x 8), rank mode (warp ballots for m <= 8, per-warp peer tables) and
+reordering (block reorder, or direct writes for ballot ranks) -- with CUDA
+events on the current stream, and installs the fastest for that workload's key
+(kind, pairs, ceil(log2 m), size class of n) with ``ms_tune_set``.  Results can
+be saved to and loaded from JSON (``tuning.json`` beside this file by default).
+
+The paper fixed its parameters per architecture by hand (Section 6,
+"Parameters"); this replaces that with a measurement on the device in use.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import _binding as B
+
+DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+
+
+def variants(log2m: int):
+    out = []
+    for shape in (0, 1, 2):
+        out.append((shape, 1, 1))
+        if log2m <= 3:
+            out += [(shape, 0, 1), (shape, 0, 0)]
+    return out
+
+
+def _time_call(fn, reps: int) -> float:
+    import torch
+
+    for _ in range(2):
+        fn()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def tune_workload(keys, vals, spec: B.BucketSpec, reps: int = 5):
+    """Times every variant for this workload, installs the fastest, returns
+    (key, best_variant, {variant: ms})."""
+    import torch
+
+    n = keys.numel()
+    log2m = (spec.m - 1).bit_length()
+    pairs = 1 if vals is not None else 0
+    sc = B.ms_tune_size_class(n)
+    kind = spec.kind if spec.m > 1 else B.RADIX
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(keys) if vals is not None else None
+    off = torch.empty(spec.m + 1, dtype=torch.int32, device=keys.device)
+    cs = spec.c()
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        if vals is None:
+            st = B.ms_multisplit_keys(keys.data_ptr(), n, cs, ko.data_ptr(), off.data_ptr(), stream)
+        else:
+            st = B.ms_multisplit_pairs(keys.data_ptr(), vals.data_ptr(), n, cs, ko.data_ptr(), vo.data_ptr(),
+                                       off.data_ptr(), stream)
+        if st != B.MS_OK:
+            raise B.MsError(st, "autotune")
+
+    times = {}
+    for v in variants(log2m):
+        B._check(B.ms_tune_set(kind, pairs, log2m, sc, *v), "ms_tune_set")
+        times[v] = _time_call(run, reps)
+    best = min(times, key=times.get)
+    B._check(B.ms_tune_set(kind, pairs, log2m, sc, *best), "ms_tune_set")
+    return (kind, pairs, log2m, sc), best, times
+
+
+def save(entries, path: str = DEFAULT_PATH):
+    """entries: list of (key, variant) pairs as returned by tune_workload."""
+    data = [{"kind": k[0], "pairs": k[1], "log2m": k[2], "size_class": k[3], "shape": v[0], "rank": v[1],
+             "reorder": v[2]} for k, v in entries]
+    with open(path, "w") as f:
+        json.dump({"format": 1, "entries": data}, f, indent=1)
+
+
+def load(path: str = DEFAULT_PATH) -> int:
+    """Installs a saved table; returns the number of entries installed (0 if absent)."""
+    if not os.path.exists(path):
+        return 0
+    with open(path) as f:
+        data = json.load(f)
+    count = 0
+    for e in data.get("entries", []):
+        st = B.ms_tune_set(e["kind"], e["pairs"], e["log2m"], e["size_class"], e["shape"], e["rank"], e["reorder"])
+        count += st == B.MS_OK
+    return count

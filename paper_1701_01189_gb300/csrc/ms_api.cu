@@ -14,7 +14,7 @@ namespace ms {
 static std::mutex g_ctx_mu;
 static DeviceCtx g_ctx[64];
 
-static ms_status to_status(cudaError_t e) {
+ms_status to_status(cudaError_t e) {
   if (e == cudaSuccess) return MS_OK;
   cudaGetLastError();  // clear a sticky launch error of this thread
   return e == cudaErrorMemoryAllocation ? MS_ERR_OUT_OF_MEMORY : MS_ERR_CUDA;
@@ -79,7 +79,7 @@ static uint32_t ceil_log2(uint32_t m) {
 }
 
 // Validates a bucket spec and converts it to kernel terms.
-static ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kind) {
+ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kind) {
   if (spec == nullptr) return MS_ERR_INVALID_ARG;
   const uint32_t m = spec->m;
   if (m < 1 || m > (uint32_t)kMaxM) return MS_ERR_INVALID_ARG;
@@ -89,6 +89,19 @@ static ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kin
   d.nbits = ceil_log2(m);
   d.m_pad = m <= 32 ? 32u : ((m + 31u) & ~31u);
   d.lut_bits = m <= 64 ? 10u : 11u;
+  if (m == 1) {
+    // every key is in bucket 0: any identifier reduces to the empty radix digit
+    if (spec->kind < MS_BUCKET_RANGE_U32 || spec->kind > MS_BUCKET_MOD) return MS_ERR_INVALID_ARG;
+    if (spec->kind == MS_BUCKET_DELTA_F32 &&
+        (!std::isfinite(spec->x0) || !std::isfinite(spec->delta) || !(spec->delta > 0.0f)))
+      return MS_ERR_INVALID_ARG;
+    if (spec->kind == MS_BUCKET_RADIX && (spec->bits != 0 || spec->shift > 32)) return MS_ERR_INVALID_ARG;
+    d.shift = 0;
+    d.mask = 0;
+    *kind = kRadix;
+    *out = d;
+    return MS_OK;
+  }
   switch (spec->kind) {
     case MS_BUCKET_RANGE_U32:
       if (m > 1 && spec->splitters == nullptr) return MS_ERR_INVALID_ARG;
@@ -127,7 +140,7 @@ static ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kin
   return MS_OK;
 }
 
-static bool overlap(const void* a, const void* b, size_t bytes) {
+bool overlap(const void* a, const void* b, size_t bytes) {
   const char* x = static_cast<const char*>(a);
   const char* y = static_cast<const char*>(b);
   return x < y + bytes && y < x + bytes;

@@ -29,13 +29,23 @@ struct Call {
   int kind;
   DevSpec sp;
   cudaStream_t stream;
+  void* ws_fixed;        // non-null: caller-provided scratch of ws_capacity bytes (no allocation, no tracing)
+  size_t ws_capacity;
 };
 
-// Tile configuration: NW warps per CTA, ITEMS keys per lane per tile.
-struct TileCfg {
-  int nw;
-  int items;
+// Kernel variant of one multisplit: post-scan tile shape (0: 8 warps x 16
+// keys, 1: 16 x 8, 2: 8 x 8), rank mode (kRankBallot only for m <= 8,
+// kRankTable) and whether the tile is reordered before the writes.
+struct Variant {
+  int shape;
+  int rank;
+  int reorder;
 };
+
+// Size class of n for tuning: 0: < 2^16, 1: < 2^20, 2: < 2^24, 3: larger.
+int size_class(uint32_t n);
+// The tuned (or default) variant for a request (ms_tune.cu).
+Variant choose_variant(const Call& c);
 
 // Runs the three stages for one request.  Defined per bucket kind in
 // ms_kind_<kind>.cu.
@@ -50,6 +60,14 @@ cudaError_t run_multisplit(const Call& c, DeviceCtx& ctx);
 // a slot (-1 when timing is off); trace_mark records event `stage` (1..3).
 int trace_begin(cudaStream_t s);
 void trace_mark(int slot, int stage, cudaStream_t s);
+
+// Shared argument handling of the C ABI (ms_api.cu).
+}  // namespace ms
+#include "ms.h"
+namespace ms {
+ms_status to_status(cudaError_t e);
+ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kind);
+bool overlap(const void* a, const void* b, size_t bytes);
 
 // Scratch from the library pool, ordered on `stream`.
 cudaError_t scratch_alloc(DeviceCtx& ctx, void** p, size_t bytes, cudaStream_t stream);

@@ -32,17 +32,14 @@
 
 namespace ms {
 
-enum RankMode : int { kRankBallot = 0, kRankTable = 1 };
-
 struct PrescanArgs {
   const uint32_t* keys;
   uint32_t n;
   DevSpec sp;
-  uint32_t tiles_per_cta;  // K: tiles of one chunk
-  uint32_t num_tiles;      // L = ceil(n / T)
-  uint32_t G;              // chunks (CTAs)
-  uint32_t* H;             // m * G, bucket-major
-  uint32_t prefetch;       // 1: bulk-prefetch the next tiles into L2
+  uint64_t chunk_elems;  // keys per chunk (the post-scan's tiles per chunk x its tile size)
+  uint32_t G;            // chunks (CTAs)
+  uint32_t* H;           // m * G, bucket-major
+  uint32_t prefetch;     // 1: bulk-prefetch the next tiles into L2
 };
 
 struct PostscanArgs {
@@ -71,79 +68,83 @@ __host__ __device__ constexpr uint32_t lut_words(uint32_t lut_bits) {
   return KIND == kRange ? (2u << lut_bits) : 0u;
 }
 
-// Adds one warp's per-lane byte counters into its 32-bit totals and clears
-// them: lane l handles buckets l, l+32, ...; a row of 32 bytes is summed with
-// four-way byte dot products.
-__device__ __forceinline__ void prescan_flush(uint8_t* wbytes, uint32_t* wtot, uint32_t m_pad, uint32_t lane) {
+// Per-lane 8-bit counters, four buckets per 32-bit word, laid out so that
+// lane l only ever touches bank l: word (q, l) = q*32 + l holds the counts of
+// buckets 4q..4q+3 seen by lane l.  A count is bumped with a shared-memory
+// atomic add of 1 << 8*(b & 3) that nothing waits for.
+//
+// Flush (before any byte can overflow): lane l sums the columns of its word
+// groups q = l, l+32, ... over the 32 lanes, reading them in a rotated order
+// so no two lanes hit one bank, and adds the four per-bucket sums into the
+// warp's 32-bit totals; then every lane zeroes its own words.
+__device__ __forceinline__ void prescan_flush(uint32_t* wwords, uint32_t* wtot, uint32_t m_pad, uint32_t lane) {
   __syncwarp();
-  for (uint32_t b = lane; b < m_pad; b += 32) {
-    uint4* row = reinterpret_cast<uint4*>(wbytes + b * 32);
-    const uint4 x = row[0], y = row[1];
-    uint32_t s = 0;
-    s = __dp4a(x.x, 0x01010101u, s);
-    s = __dp4a(x.y, 0x01010101u, s);
-    s = __dp4a(x.z, 0x01010101u, s);
-    s = __dp4a(x.w, 0x01010101u, s);
-    s = __dp4a(y.x, 0x01010101u, s);
-    s = __dp4a(y.y, 0x01010101u, s);
-    s = __dp4a(y.z, 0x01010101u, s);
-    s = __dp4a(y.w, 0x01010101u, s);
-    wtot[b] += s;
-    row[0] = make_uint4(0u, 0u, 0u, 0u);
-    row[1] = make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t groups = m_pad >> 2;
+  for (uint32_t q = lane; q < groups; q += 32) {
+    uint32_t lo = 0, hi = 0;  // 16-bit lanes: buckets (4q, 4q+2) and (4q+1, 4q+3)
+#pragma unroll 8
+    for (uint32_t s = 0; s < 32; ++s) {
+      const uint32_t v = wwords[q * 32 + ((lane + s) & 31u)];
+      lo += v & 0x00ff00ffu;
+      hi += (v >> 8) & 0x00ff00ffu;
+    }
+    wtot[4 * q + 0] += lo & 0xffffu;
+    wtot[4 * q + 1] += hi & 0xffffu;
+    wtot[4 * q + 2] += lo >> 16;
+    wtot[4 * q + 3] += hi >> 16;
   }
+  __syncwarp();
+  for (uint32_t q = 0; q < groups; ++q) wwords[q * 32 + lane] = 0u;
   __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
 // Pre-scan.  Dynamic shared memory (words): splitter table (256), LUT, then
-// per warp m_pad x 32 byte counters (m_pad * 8 words), then per warp m_pad
-// 32-bit totals.
-template <int KIND, int NB, int NW, int ITEMS>
-__global__ void __launch_bounds__(NW * 32, 3) k_prescan(PrescanArgs a) {
+// per warp m_pad * 8 words of byte counters, then per warp m_pad 32-bit totals.
+template <int KIND, int NB, int NW, int ITEMS, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_prescan(PrescanArgs a) {
   constexpr int T = NW * 32 * ITEMS;
   extern __shared__ __align__(16) uint32_t smem[];
   const DevSpec& sp = a.sp;
   const uint32_t m_pad = sp.m_pad;
   uint32_t* s_tbl = smem;
   uint2* s_lut = reinterpret_cast<uint2*>(smem + 256);
-  uint32_t* s_bytes = smem + 256 + lut_words<KIND>(sp.lut_bits);  // NW * m_pad * 8 words
-  uint32_t* s_tot = s_bytes + NW * m_pad * 8;                      // NW * m_pad words
+  uint32_t* s_words = smem + 256 + lut_words<KIND>(sp.lut_bits);  // NW * m_pad * 8 words
+  uint32_t* s_tot = s_words + NW * m_pad * 8;                      // NW * m_pad words
 
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
-  uint8_t* wbytes = reinterpret_cast<uint8_t*>(s_bytes + w * m_pad * 8);  // [b][lane]
+  uint32_t* wwords = s_words + w * m_pad * 8;
   uint32_t* wtot = s_tot + w * m_pad;
-  for (uint32_t i = threadIdx.x; i < NW * m_pad * 9; i += NW * 32) s_bytes[i] = 0u;  // bytes + totals
+  for (uint32_t i = threadIdx.x; i < NW * m_pad * 9; i += NW * 32) s_words[i] = 0u;  // counters + totals
   build_bucket_tables<KIND, NB>(sp, s_tbl, s_lut);  // ends with a barrier
 
   const uint32_t c = blockIdx.x;
-  const uint32_t t0 = c * a.tiles_per_cta;
-  const uint32_t t1 = min(t0 + a.tiles_per_cta, a.num_tiles);
+  const size_t begin = (size_t)c * a.chunk_elems;
+  const size_t end = min((size_t)a.n, begin + a.chunk_elems);
   uint32_t since_flush = 0;  // keys counted per lane since the last flush
-  for (uint32_t tile = t0; tile < t1; ++tile) {
-    if (a.prefetch && threadIdx.x == 0 && tile + 2 < t1 && (size_t)(tile + 3) * T <= a.n)
-      prefetch_l2(a.keys + (size_t)(tile + 2) * T, T * 4u);  // a full tile only
-    const uint32_t* src = a.keys + (size_t)tile * T;
-    const uint32_t rem = (uint32_t)min((size_t)T, (size_t)a.n - (size_t)tile * T);
+  for (size_t tb = begin; tb < end; tb += T) {
+    if (a.prefetch && threadIdx.x == 0 && tb + 3 * (size_t)T <= end)
+      prefetch_l2(a.keys + tb + 2 * (size_t)T, T * 4u);  // a full tile only
+    const uint32_t* src = a.keys + tb;
+    const uint32_t rem = (uint32_t)min((size_t)T, end - tb);
     const uint32_t off0 = w * (32 * ITEMS) + lane;
     uint32_t key[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) key[i] = (off0 + i * 32 < rem) ? src[off0 + i * 32] : 0u;
     if (since_flush + ITEMS > 255u) {
-      prescan_flush(wbytes, wtot, m_pad, lane);
+      prescan_flush(wwords, wtot, m_pad, lane);
       since_flush = 0;
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       if (off0 + i * 32 < rem) {
         const uint32_t b = bucket_of<KIND, NB>(key[i], sp, s_tbl, s_lut);
-        uint8_t* p = wbytes + b * 32 + lane;
-        *p = (uint8_t)(*p + 1u);
+        atomicAdd(wwords + ((b >> 2) << 5) + lane, 1u << ((b & 3u) << 3));
       }
     }
     since_flush += ITEMS;
   }
-  prescan_flush(wbytes, wtot, m_pad, lane);
+  prescan_flush(wwords, wtot, m_pad, lane);
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < sp.m; b += NW * 32) {
     uint32_t s = 0;
@@ -160,15 +161,21 @@ __host__ size_t prescan_smem_bytes(uint32_t m_pad, uint32_t lut_bits) {
 
 // ---------------------------------------------------------------------------
 // Post-scan.  Dynamic shared memory (words): splitter table (256), LUT,
-// s_run / s_delta (256 each), s_warp (32), counters NW*(m_pad+1), peer tables
-// NW*m_pad (table mode), then the reorder buffers: T keys, T values (pairs),
-// T bucket bytes.
-template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK>
-__global__ void __launch_bounds__(NW * 32, PAIRS ? 2 : 3) k_postscan(PostscanArgs a) {
+// s_run / s_delta (256 each), s_warp (32), counters NW*(m_pad+1), two peer
+// tables per warp 2*NW*m_pad (table mode), then (block reorder) the reorder
+// buffers: T keys, T values (pairs), T bucket bytes.
+//
+// REORDER = 1: the block-level reordering of Section 5.6.2 (writes coalesced
+// per bucket run).  REORDER = 0: each key goes straight from its registers to
+// its final position (the no-reorder design of Section 5.3's DMS), which for
+// a few buckets already gives runs of consecutive addresses per warp store.
+template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   constexpr int THREADS = NW * 32;
   constexpr int T = THREADS * ITEMS;
   static_assert(NW >= 8, "the per-bucket phase needs >= 256 threads");
   static_assert(NW == 8 || NW == 16 || NW == 32, "NW must be 8, 16 or 32");
+  static_assert(RANK == kRankTable || NB <= 5, "ballot ranks need m <= 32");
   constexpr int LOGNW = NW == 8 ? 3 : NW == 16 ? 4 : 5;
   extern __shared__ __align__(16) uint32_t smem[];
   const DevSpec& sp = a.sp;
@@ -178,17 +185,17 @@ __global__ void __launch_bounds__(NW * 32, PAIRS ? 2 : 3) k_postscan(PostscanArg
   uint32_t* s_run = smem + 256 + lut_words<KIND>(sp.lut_bits);
   uint32_t* s_delta = s_run + 256;
   uint32_t* s_warp = s_delta + 256;
-  uint32_t* s_cnt = s_warp + 32;                                       // [w * S + b]
-  uint32_t* s_peer = s_cnt + NW * S;                                   // [w * m_pad + b]
-  uint32_t* s_keys = s_peer + (RANK == kRankTable ? NW * m_pad : 0u);  // T
-  uint32_t* s_vals = s_keys + T;                                       // T (pairs)
+  uint32_t* s_cnt = s_warp + 32;                                           // [w * S + b]
+  uint32_t* s_peer = s_cnt + NW * S;                                       // [w][2][m_pad]
+  uint32_t* s_keys = s_peer + (RANK == kRankTable ? 2 * NW * m_pad : 0u);  // T
+  uint32_t* s_vals = s_keys + T;                                           // T (pairs)
   uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + T * (PAIRS ? 2 : 1));
 
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   const uint32_t c = blockIdx.x;
   const uint32_t len = m * a.G;
   if (RANK == kRankTable)
-    for (uint32_t i = threadIdx.x; i < NW * m_pad; i += THREADS) s_peer[i] = 0u;
+    for (uint32_t i = threadIdx.x; i < 2 * NW * m_pad; i += THREADS) s_peer[i] = 0u;
   // next global position of each bucket: chunk start (forward) or chunk end (reverse)
   for (uint32_t b = threadIdx.x; b < m; b += THREADS) {
     const uint32_t e = b * a.G + c;
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(NW * 32, PAIRS ? 2 : 3) k_postscan(PostscanArg
   build_bucket_tables<KIND, NB>(sp, s_tbl, s_lut);  // ends with a barrier
 
   uint32_t* wc = s_cnt + w * S;
-  uint32_t* wpeer = s_peer + w * m_pad;
+  uint32_t* wpeer = s_peer + w * 2 * m_pad;
   const uint32_t lt_mask = lanemask_lt();
   // Alg. 2: per ballot, the mask that keeps the lanes whose bucket bit equals
   // the same bit of this lane's id
@@ -229,8 +236,10 @@ __global__ void __launch_bounds__(NW * 32, PAIRS ? 2 : 3) k_postscan(PostscanArg
       key[i] = valid ? __ldcs(ksrc + off0 + i * 32) : 0u;
       if constexpr (PAIRS) val[i] = valid ? __ldcs(vsrc + off0 + i * 32) : 0u;
     }
-    for (uint32_t b = lane; b < m_pad; b += 32) wc[b] = 0u;
-    __syncwarp();
+    if constexpr (RANK == kRankTable) {
+      for (uint32_t b = lane; b < m_pad; b += 32) wc[b] = 0u;
+      __syncwarp();
+    }
     uint32_t run = 0;  // ballot mode: keys of bucket `lane` in earlier windows of this warp
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -251,19 +260,20 @@ __global__ void __launch_bounds__(NW * 32, PAIRS ? 2 : 3) k_postscan(PostscanArg
         rb[i] = (before + __popc(own & lt_mask)) | (b << 16);
         run += __popc(lane_bm);
       } else {
-        // peer table: OR the lane bit into the bucket's entry, read the peers
-        if (valid) atomicOr(wpeer + b, 1u << lane);
+        // peer table (two, alternating by window): OR the lane bit into the
+        // bucket's entry, read the peers back; the lowest peer advances the
+        // warp's counter of the bucket and clears the entry.
+        uint32_t* tbl = wpeer + (i & 1) * m_pad;
+        if (valid) atomicOr(tbl + b, 1u << lane);
         __syncwarp();
-        const uint32_t own = valid ? wpeer[b] : 0u;
+        const uint32_t own = valid ? tbl[b] : 0u;
         __syncwarp();
         const uint32_t lt = own & lt_mask;
         uint32_t before = 0;
-        if (valid && lt == 0u) {  // lowest peer: advance the counter, clear the entry
-          before = wc[b];
-          wc[b] = before + __popc(own);
-          wpeer[b] = 0u;
+        if (valid && lt == 0u) {
+          before = atomicAdd(wc + b, (uint32_t)__popc(own));
+          tbl[b] = 0u;
         }
-        __syncwarp();
         before = __shfl_sync(kFull, before, (__ffs(own) - 1) & 31);
         rb[i] = (before + __popc(lt)) | (b << 16);
       }
@@ -298,8 +308,7 @@ __global__ void __launch_bounds__(NW * 32, PAIRS ? 2 : 3) k_postscan(PostscanArg
     }
     __syncthreads();
 
-    // Reorder the tile (a local stable multisplit) and compute, per bucket,
-    // global position minus tile position.
+    // Per bucket: global position minus tile position.
     if (threadIdx.x < m) {
       const uint32_t b = threadIdx.x;
       const uint32_t tstart = s_cnt[b];
@@ -314,44 +323,61 @@ __global__ void __launch_bounds__(NW * 32, PAIRS ? 2 : 3) k_postscan(PostscanArg
       }
       s_delta[b] = g - tstart;
     }
+    if constexpr (REORDER) {
+      // Reorder the tile (a local stable multisplit of Section 4.7).
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      if (off0 + i * 32 < tile_n) {
-        const uint32_t b = rb[i] >> 16;
-        const uint32_t p = wc[b] + (rb[i] & 0xffffu);
-        if (p < (uint32_t)T) {
-          s_keys[p] = key[i];
-          if constexpr (PAIRS) s_vals[p] = val[i];
-          s_bkt[p] = (uint8_t)b;
+      for (int i = 0; i < ITEMS; ++i) {
+        if (off0 + i * 32 < tile_n) {
+          const uint32_t b = rb[i] >> 16;
+          const uint32_t p = wc[b] + (rb[i] & 0xffffu);
+          if (p < (uint32_t)T) {
+            s_keys[p] = key[i];
+            if constexpr (PAIRS) s_vals[p] = val[i];
+            s_bkt[p] = (uint8_t)b;
+          } else {
+            atomicOr(a.err, kDevErrBounds);
+          }
+        }
+      }
+      __syncthreads();
+      // Consecutive threads hold consecutive keys of one bucket run: the
+      // global writes are coalesced per run.
+#pragma unroll 4
+      for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
+        const uint32_t g = s_delta[s_bkt[p]] + p;
+        if (g < a.n) {
+          __stcs(a.keys_out + g, s_keys[p]);
+          if constexpr (PAIRS) __stcs(a.vals_out + g, s_vals[p]);
         } else {
           atomicOr(a.err, kDevErrBounds);
         }
       }
-    }
-    __syncthreads();
-
-    // Consecutive threads hold consecutive keys of one bucket run: the global
-    // writes are coalesced per run.
-#pragma unroll 4
-    for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
-      const uint32_t g = s_delta[s_bkt[p]] + p;
-      if (g < a.n) {
-        __stcs(a.keys_out + g, s_keys[p]);
-        if constexpr (PAIRS) __stcs(a.vals_out + g, s_vals[p]);
-      } else {
-        atomicOr(a.err, kDevErrBounds);
+    } else {
+      __syncthreads();  // s_delta ready
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        if (off0 + i * 32 < tile_n) {
+          const uint32_t b = rb[i] >> 16;
+          const uint32_t g = s_delta[b] + wc[b] + (rb[i] & 0xffffu);
+          if (g < a.n) {
+            __stcs(a.keys_out + g, key[i]);
+            if constexpr (PAIRS) __stcs(a.vals_out + g, val[i]);
+          } else {
+            atomicOr(a.err, kDevErrBounds);
+          }
+        }
       }
     }
     __syncthreads();
   }
 }
 
-template <int KIND, int NW, int ITEMS, bool PAIRS, int RANK>
+template <int KIND, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER>
 __host__ size_t postscan_smem_bytes(uint32_t m_pad, uint32_t lut_bits) {
   constexpr uint32_t T = NW * 32 * ITEMS;
   return 4u * (256u + lut_words<KIND>(lut_bits) + 256u + 256u + 32u + NW * (m_pad + 1u) +
-               (RANK == kRankTable ? NW * m_pad : 0u) + T * (PAIRS ? 2u : 1u)) +
-         T;
+               (RANK == kRankTable ? 2 * NW * m_pad : 0u) + (REORDER ? T * (PAIRS ? 2u : 1u) : 0u)) +
+         (REORDER ? T : 0u);
 }
 
 }  // namespace ms

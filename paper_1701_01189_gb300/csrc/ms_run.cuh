@@ -52,25 +52,30 @@ static inline Chunking make_chunking(uint32_t n, uint32_t T, uint32_t max_ctas) 
   return ch;
 }
 
-template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK>
+// Pre-scan tile: 8 warps x 16 keys per lane.  Its NB only sizes the splitter
+// search of range buckets; 8 covers every m.
+constexpr int kPreNW = 8, kPreItems = 16, kPreMinB = 3;
+
+template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int MINB>
 static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   constexpr int THREADS = NW * 32;
   constexpr uint32_t T = THREADS * ITEMS;
-  auto kpre = k_prescan<KIND, NB, NW, ITEMS>;
-  auto kpost = k_postscan<KIND, NB, NW, ITEMS, PAIRS, RANK>;
+  constexpr int NBPRE = KIND == kRange ? 8 : 0;
+  auto kpre = k_prescan<KIND, NBPRE, kPreNW, kPreItems, kPreMinB>;
+  auto kpost = k_postscan<KIND, NB, NW, ITEMS, PAIRS, RANK, REORDER, MINB>;
   const uint32_t m_pad = c.sp.m_pad, lb = c.sp.lut_bits;
-  // shared memory is sized for the largest m of this instantiation so the
-  // occupancy query is made once
-  const uint32_t mp_max = (KIND == kRadix || RANK == kRankBallot) ? (NB <= 5 ? 32u : (1u << NB)) : 256u;
-  const size_t smem_pre_max = prescan_smem_bytes<KIND, NW>(mp_max, 11);
-  const size_t smem_post_max = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK>(mp_max, 11);
-  const size_t smem_pre = prescan_smem_bytes<KIND, NW>(m_pad, lb);
-  const size_t smem_post = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK>(m_pad, lb);
+  const uint32_t mp_max = RANK == kRankBallot ? 32u : 256u;
+  const size_t smem_pre_max = prescan_smem_bytes<KIND, kPreNW>(256, 11);
+  const size_t smem_post_max = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER>(mp_max, 11);
+  const size_t smem_pre = prescan_smem_bytes<KIND, kPreNW>(m_pad, lb);
+  const size_t smem_post = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER>(m_pad, lb);
   static LaunchInfo li_pre, li_post;
   const int nb_post = setup_kernel(li_post, kpost, THREADS, smem_post_max, smem_post, ctx.device);
-  const int nb_pre = setup_kernel(li_pre, kpre, THREADS, smem_pre_max, smem_pre, ctx.device);
+  const int nb_pre = setup_kernel(li_pre, kpre, kPreNW * 32, smem_pre_max, smem_pre, ctx.device);
 
-  const int resident = nb_post < nb_pre ? nb_post : nb_pre;
+  // One chunk per CTA in both kernels; the pre-scan CTAs walk the same chunks
+  // of K*T keys with their own tile size.
+  const int resident = std::min(nb_post, nb_pre);
   const Chunking ch = make_chunking(c.n, T, (uint32_t)(ctx.sm_count * resident));
   const uint32_t m = c.sp.m;
   const uint32_t len = m * ch.G;
@@ -81,18 +86,25 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   const size_t st_bytes = (size_t)nscan * 8;
   const size_t bytes = h_bytes + st_bytes + 16;
   void* ws = nullptr;
-  cudaError_t e = scratch_alloc(ctx, &ws, bytes, c.stream);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (c.ws_fixed != nullptr) {
+    if (bytes > c.ws_capacity) return cudaErrorMemoryAllocation;
+    ws = c.ws_fixed;
+  } else {
+    e = scratch_alloc(ctx, &ws, bytes, c.stream);
+    if (e != cudaSuccess) return e;
+  }
   uint32_t* H = static_cast<uint32_t*>(ws);
   auto* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + h_bytes);
   auto* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes);
   e = cudaMemsetAsync(status, 0, st_bytes + 16, c.stream);
 
-  const uint32_t aligned = ((reinterpret_cast<uintptr_t>(c.keys_in) | reinterpret_cast<uintptr_t>(c.vals_in)) & 15u) == 0;
-  const int slot = trace_begin(c.stream);
+  const uint32_t aligned =
+      ((reinterpret_cast<uintptr_t>(c.keys_in) | reinterpret_cast<uintptr_t>(c.vals_in)) & 15u) == 0;
+  const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
   if (e == cudaSuccess) {
-    PrescanArgs pa{c.keys_in, c.n, c.sp, ch.K, ch.L, ch.G, H, aligned};
-    kpre<<<ch.G, THREADS, smem_pre, c.stream>>>(pa);
+    PrescanArgs pa{c.keys_in, c.n, c.sp, (uint64_t)ch.K * T, ch.G, H, aligned};
+    kpre<<<ch.G, kPreNW * 32, smem_pre, c.stream>>>(pa);
     e = cudaGetLastError();
     trace_mark(slot, 1, c.stream);
   }
@@ -108,35 +120,47 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
     e = cudaGetLastError();
     trace_mark(slot, 3, c.stream);
   }
-  const cudaError_t e2 = scratch_free(ws, c.stream);
+  const cudaError_t e2 = c.ws_fixed != nullptr ? cudaSuccess : scratch_free(ws, c.stream);
   return e != cudaSuccess ? e : e2;
 }
 
-// Tile: 8 warps x 32 lanes x 16 keys = 4096 keys.  Ranks by ballots for m <= 4
-// (one or two ballots per window), by the peer table otherwise.
-template <int KIND, int NB>
-static cudaError_t run_ms_nb(const Call& c, DeviceCtx& ctx) {
-  constexpr int RANK = NB <= 2 ? kRankBallot : kRankTable;
-  // identifiers other than range splitters do not depend on NB in table mode:
-  // share one instantiation
-  constexpr int NBK = (KIND == kRange || RANK == kRankBallot) ? NB : 8;
-  if (c.vals_in != nullptr) return run_ms_cfg<KIND, NBK, 8, 16, true, RANK>(c, ctx);
-  return run_ms_cfg<KIND, NBK, 8, 16, false, RANK>(c, ctx);
+// Tile shapes of the post-scan the tuner chooses from (warps x keys per lane):
+// 0: 8 x 16 (4096 keys), 1: 16 x 8 (4096 keys), 2: 8 x 8 (2048 keys).
+template <int KIND, int NB, bool PAIRS, int RANK, int REORDER>
+static cudaError_t run_ms_shape(const Call& c, DeviceCtx& ctx, int shape) {
+  switch (shape) {
+    case 1: return run_ms_cfg<KIND, NB, 16, 8, PAIRS, RANK, REORDER, PAIRS ? 1 : 2>(c, ctx);
+    case 2: return run_ms_cfg<KIND, NB, 8, 8, PAIRS, RANK, REORDER, PAIRS ? 3 : 4>(c, ctx);
+    default: return run_ms_cfg<KIND, NB, 8, 16, PAIRS, RANK, REORDER, PAIRS ? 2 : 3>(c, ctx);
+  }
 }
 
+template <int KIND, int NB, int RANK, int REORDER>
+static cudaError_t run_ms_pairs(const Call& c, DeviceCtx& ctx, int shape) {
+  if (c.vals_in != nullptr) return run_ms_shape<KIND, NB, true, RANK, REORDER>(c, ctx, shape);
+  return run_ms_shape<KIND, NB, false, RANK, REORDER>(c, ctx, shape);
+}
+
+template <int KIND, int NB>
+static cudaError_t run_ms_ballot(const Call& c, DeviceCtx& ctx, const Variant& v) {
+  if (v.reorder) return run_ms_pairs<KIND, NB, kRankBallot, 1>(c, ctx, v.shape);
+  return run_ms_pairs<KIND, NB, kRankBallot, 0>(c, ctx, v.shape);
+}
+
+// Ballot ranks are built for m <= 8 (NB <= 3); every m runs with peer tables
+// (NB = 8 sizes the range-splitter search for any m).
 template <int KIND>
 static cudaError_t run_ms_kind(const Call& c, DeviceCtx& ctx) {
-  switch (c.sp.nbits) {
-    case 0: return run_ms_nb<KIND, 0>(c, ctx);
-    case 1: return run_ms_nb<KIND, 1>(c, ctx);
-    case 2: return run_ms_nb<KIND, 2>(c, ctx);
-    case 3: return run_ms_nb<KIND, 3>(c, ctx);
-    case 4: return run_ms_nb<KIND, 4>(c, ctx);
-    case 5: return run_ms_nb<KIND, 5>(c, ctx);
-    case 6: return run_ms_nb<KIND, 6>(c, ctx);
-    case 7: return run_ms_nb<KIND, 7>(c, ctx);
-    default: return run_ms_nb<KIND, 8>(c, ctx);
+  const Variant v = choose_variant(c);
+  if (v.rank == kRankBallot && c.sp.nbits <= 3) {
+    switch (c.sp.nbits) {
+      case 0: return run_ms_ballot<KIND, 0>(c, ctx, v);
+      case 1: return run_ms_ballot<KIND, 1>(c, ctx, v);
+      case 2: return run_ms_ballot<KIND, 2>(c, ctx, v);
+      default: return run_ms_ballot<KIND, 3>(c, ctx, v);
+    }
   }
+  return run_ms_pairs<KIND, 8, kRankTable, 1>(c, ctx, v.shape);
 }
 
 }  // namespace ms

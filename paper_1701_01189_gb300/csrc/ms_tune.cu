@@ -1,0 +1,82 @@
+// ms_tune.cu -- the variant table consulted by every multisplit: which tile
+// shape, rank mode and reordering to run for (bucket kind, keys or pairs,
+// ceil(log2 m), size class of n).  Defaults come from the rules below; the
+// autotuner (paper_1701_01189_gb300/autotune.py) measures the candidates on the
+// device and installs the fastest with ms_tune_set().
+#include <mutex>
+
+#include "ms.h"
+#include "ms_host.h"
+
+namespace ms {
+
+namespace {
+constexpr int kKinds = 4, kNbits = 9, kClasses = 4;
+std::mutex g_mu;
+bool g_set[kKinds][2][kNbits][kClasses] = {};
+Variant g_table[kKinds][2][kNbits][kClasses];
+
+Variant default_variant(int nbits) {
+  Variant v;
+  v.shape = 0;
+  v.rank = nbits <= 2 ? kRankBallot : kRankTable;  // ballots are cheap for up to 4 buckets
+  v.reorder = nbits == 0 ? 0 : 1;                  // one bucket: a plain copy, already coalesced
+  return v;
+}
+}  // namespace
+
+int size_class(uint32_t n) {
+  if (n < (1u << 16)) return 0;
+  if (n < (1u << 20)) return 1;
+  if (n < (1u << 24)) return 2;
+  return 3;
+}
+
+Variant choose_variant(const Call& c) {
+  const int nb = (int)c.sp.nbits, pairs = c.vals_in != nullptr ? 1 : 0, sc = size_class(c.n);
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (c.kind >= 0 && c.kind < kKinds && nb < kNbits && g_set[c.kind][pairs][nb][sc]) return g_table[c.kind][pairs][nb][sc];
+  return default_variant(nb);
+}
+
+}  // namespace ms
+
+using namespace ms;
+
+extern "C" int ms_tune_size_class(size_t n) { return n >= ((size_t)1 << 32) ? 3 : size_class((uint32_t)n); }
+
+extern "C" ms_status ms_tune_set(int kind, int pairs, int nbits, int sclass, int shape, int rank, int reorder) {
+  if (kind < 0 || kind >= kKinds || pairs < 0 || pairs > 1 || nbits < 0 || nbits >= kNbits || sclass < 0 ||
+      sclass >= kClasses || shape < 0 || shape > 2 || rank < 0 || rank > 1 || reorder < 0 || reorder > 1)
+    return MS_ERR_INVALID_ARG;
+  if (rank == kRankBallot && nbits > 3) return MS_ERR_INVALID_ARG;
+  if (rank == kRankTable && reorder == 0) return MS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_table[kind][pairs][nbits][sclass] = Variant{shape, rank, reorder};
+  g_set[kind][pairs][nbits][sclass] = true;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_tune_get(int kind, int pairs, int nbits, int sclass, int* shape, int* rank, int* reorder) {
+  if (kind < 0 || kind >= kKinds || pairs < 0 || pairs > 1 || nbits < 0 || nbits >= kNbits || sclass < 0 ||
+      sclass >= kClasses)
+    return MS_ERR_INVALID_ARG;
+  Variant v;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    v = g_set[kind][pairs][nbits][sclass] ? g_table[kind][pairs][nbits][sclass] : default_variant(nbits);
+  }
+  if (shape) *shape = v.shape;
+  if (rank) *rank = v.rank;
+  if (reorder) *reorder = v.reorder;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_tune_reset(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  for (auto& a : g_set)
+    for (auto& b : a)
+      for (auto& c : b)
+        for (auto& d : c) d = false;
+  return MS_OK;
+}

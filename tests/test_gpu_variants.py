@@ -1,0 +1,58 @@
+"""Parameter invariance: every kernel variant the tuner can choose (tile shape,
+rank mode, reordering) gives the oracle's result bit for bit."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from parity import Case, check_multisplit
+
+pytestmark = pytest.mark.gpu
+
+
+def variants(log2m):
+    out = []
+    for shape in (0, 1, 2):
+        out.append((shape, 1, 1))
+        if log2m <= 3:
+            out += [(shape, 0, 1), (shape, 0, 0)]
+    return out
+
+
+CASES = []
+for m, kind in itertools.product([1, 2, 3, 8, 33, 256], ["range", "mod", "radix", "delta"]):
+    if kind == "radix" and m & (m - 1):
+        continue
+    CASES.append((kind, m))
+
+
+def make_case(kind, m):
+    if kind == "range":
+        return Case(oracle.RANGE_U32, m, splitters=synthetic.range_splitters(m, m))
+    if kind == "mod":
+        return Case(oracle.MOD, m)
+    if kind == "radix":
+        bits = m.bit_length() - 1
+        return Case(oracle.RADIX, m, shift=32 - max(bits, 1) if bits else 0, bits=bits)
+    return Case(oracle.DELTA_F32, m, x0=0.0, delta=float(np.float32(1000.0) / np.float32(m)))
+
+
+@pytest.mark.parametrize("kind,m", CASES, ids=[f"{k}-m{m}" for k, m in CASES])
+def test_every_variant_matches_oracle(kind, m):
+    import paper_1701_01189_gb300 as ms
+
+    case = make_case(kind, m)
+    log2m = (m - 1).bit_length()
+    n = 3 * 4096 + 129
+    keys = synthetic.uniform_f32_1000(n, 3) if kind == "delta" else synthetic.uniform_u32(n, 3)
+    try:
+        for shape, rank, reorder in variants(log2m):
+            for pairs in (0, 1):
+                assert ms.ms_tune_set(case.kind, pairs, log2m, ms.ms_tune_size_class(n), shape, rank,
+                                      reorder) == ms.MS_OK
+            check_multisplit(keys, None, case)
+            check_multisplit(keys, synthetic.index_values(n), case)
+    finally:
+        ms.ms_tune_reset()
