@@ -99,6 +99,29 @@ ms_status ms_multisplit_pairs(const uint32_t *keys_in, const uint32_t *vals_in, 
 ms_status ms_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, size_t n, int begin_bit,
                         int end_bit, uint32_t *keys_out, uint32_t *vals_out, void *stream);
 
+/* Keys-only stable multisplit that allocates nothing (the paper has no
+ * counterpart; this is a deployment variant of ms_multisplit_keys).  For
+ * callers that must not allocate device memory during the call: work being
+ * captured into a CUDA graph without allocation nodes, hot loops that forbid
+ * allocator calls, or processes whose device memory is owned by another
+ * allocator.  Same arguments, result and argument errors as
+ * ms_multisplit_keys; the scratch comes from a fixed 1 MiB array in device
+ * memory that every GPU loading the library holds until exit.
+ *   - The first call on each device (with it current) looks up the array's
+ *     device address and sets up the kernels; make it before any stream
+ *     capture.  It allocates nothing.
+ *   - All calls share the array: calls that overlap on the GPU race and
+ *     corrupt each other's results; serialize them (one stream, or events).
+ *   - The scratch must hold 4*m*G + 8*ceil(m*G/4096) + 16 bytes (G = CTAs of
+ *     the launch, at most SMs x resident CTAs per SM; about 610 KiB at most on
+ *     a 152-SM GB300).  A call needing more gets MS_ERR_OUT_OF_MEMORY and
+ *     nothing is enqueued.
+ *   - Device-side failures (an expired bounded wait, a failed bounds check)
+ *     are recorded in a word of the fixed array and are not reported by
+ *     ms_device_status(). */
+ms_status ms_multisplit_keys_noalloc(const uint32_t *keys_in, size_t n, const ms_bucket_spec *spec,
+                                     uint32_t *keys_out, uint32_t *offsets, void *stream);
+
 /* Reads and clears the calling device's status word: MS_OK, or
  * MS_ERR_TIMEOUT if any bounded device-side wait expired since the last read.
  * Synchronizes `stream` first. */

@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         SP = ctypes.POINTER(_Spec)
         L.ms_multisplit_keys.argtypes = [P, S, SP, P, P, P]
         L.ms_multisplit_pairs.argtypes = [P, P, S, SP, P, P, P, P]
+        L.ms_multisplit_keys_noalloc.argtypes = [P, S, SP, P, P, P]
         L.ms_radix_sort.argtypes = [P, P, S, I, I, P, P, P]
         L.ms_device_status.argtypes = [P]
         L.ms_status_string.argtypes = [I]
@@ -78,7 +79,8 @@ def lib() -> ctypes.CDLL:
         L.ms_test_expire_lookback.restype = ctypes.c_int
         L.ms_stage_timing.argtypes = [I]
         L.ms_stage_times.argtypes = [P, P, P, P]
-        for f in ("ms_multisplit_keys", "ms_multisplit_pairs", "ms_radix_sort", "ms_device_status",
+        for f in ("ms_multisplit_keys", "ms_multisplit_pairs", "ms_multisplit_keys_noalloc", "ms_radix_sort",
+                  "ms_device_status",
                   "ms_stage_timing", "ms_stage_times"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -93,6 +95,11 @@ def ms_multisplit_keys(keys_in: int, n: int, spec: "_Spec", keys_out: int, offse
 def ms_multisplit_pairs(keys_in: int, vals_in: int, n: int, spec: "_Spec", keys_out: int, vals_out: int,
                         offsets: int, stream: int) -> int:
     return lib().ms_multisplit_pairs(keys_in, vals_in, n, ctypes.byref(spec), keys_out, vals_out, offsets, stream)
+
+
+def ms_multisplit_keys_noalloc(keys_in: int, n: int, spec: "_Spec", keys_out: int, offsets: int,
+                               stream: int) -> int:
+    return lib().ms_multisplit_keys_noalloc(keys_in, n, ctypes.byref(spec), keys_out, offsets, stream)
 
 
 def ms_radix_sort(keys_in: int, vals_in: int, n: int, begin_bit: int, end_bit: int, keys_out: int,
