@@ -174,6 +174,9 @@ def run_gpu(args, rank: int, world: int):
     if world > 1:
         torch.distributed.barrier()
     ms.lib()
+    from paper_1701_01189_gb300 import autotune
+
+    autotune.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     n = 1 << args.n_log2
     hk, hspl, hvals = make_inputs(n)
@@ -294,6 +297,10 @@ def run_gpu(args, rank: int, world: int):
 
     if not args.no_e2e:
         result["e2e"] = e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n, world)
+    del dkeys, dk, dspl, dvals, out_k, out_v
+    torch.cuda.empty_cache()
+    if not args.no_extras:
+        result["extras"] = extras_gpu(args, ms, metrics, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(hk, hspl, hvals, case_list, n, budget_s=args.cpu_budget)
     return result
@@ -361,6 +368,108 @@ def e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n,
     value = metrics.rate_g(n * len(case_list) * steps * world, ms_total * 1e-3)
     return {"value": round(value, 3), "unit": "G elements/s (keys or pairs)",
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps}
+
+
+# ----------------------------------------------------------------------------- other configurations
+def _time(torch, fn, reps: int, warmup: int = 2) -> float:
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def extras_gpu(args, ms, metrics, torch, dev):
+    """The radix-sort and batched configurations, timed after the main step (not in `value`)."""
+    peak, _ = measured_peaks()
+    out = {}
+
+    def dev_u32(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+
+    # LSD radix sort: n = 2^28 keys (and pairs), 4 passes; n = 2^24 keys of 16 random bits, 2 passes
+    for name, n, bits, pairs in (("sort_2p28_keys", 1 << 28, 32, False), ("sort_2p28_pairs", 1 << 28, 32, True),
+                                 ("sort_2p24_16bit_keys", 1 << 24, 16, False),
+                                 ("sort_2p24_16bit_pairs", 1 << 24, 16, True)):
+        keys = dev_u32(synthetic.uniform_u32_bits(n, bits, 7) if bits < 32 else synthetic.uniform_u32(n, 7))
+        vals = dev_u32(synthetic.uniform_u32(n, 8)) if pairs else None
+        ko = torch.empty_like(keys)
+        vo = torch.empty_like(keys) if pairs else None
+        sptr = torch.cuda.current_stream().cuda_stream
+
+        def run():
+            st = ms.ms_radix_sort(keys.data_ptr(), vals.data_ptr() if pairs else None, n, 0, bits, ko.data_ptr(),
+                                  vo.data_ptr() if pairs else None, sptr)
+            if st != ms.MS_OK:
+                raise ms.MsError(st, name)
+
+        t = _time(torch, run, reps=5)
+        passes = (bits + 7) // 8
+        rate = metrics.rate_g(n, t * 1e-3)
+        comp = metrics.sol_rate_g(peak, metrics.sort_compulsory_bytes_per_element(pairs, passes))
+        out[name] = {"ms": round(t, 4), ("gpairs_s" if pairs else "gkeys_s"): round(rate, 2),
+                     "frac_compulsory_roofline": round(rate / comp, 4), "passes": passes}
+        del keys, vals, ko, vo
+    torch.cuda.empty_cache()
+
+    # batched: 4096 segments, sizes floor(2^U), U ~ U(8, 20), key mod 32, pairs (value = index)
+    sizes = synthetic.segment_sizes(4096, 8, 20, 2024)
+    total = int(sizes.sum())
+    kall = dev_u32(synthetic.uniform_u32(total, 2025))
+    vall = torch.empty_like(kall)
+    ko_all, vo_all = torch.empty_like(kall), torch.empty_like(kall)
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    for st_, n_ in zip(starts, sizes):  # value = index within the segment
+        vall[int(st_):int(st_ + n_)] = torch.arange(int(n_), dtype=torch.int32, device=dev)
+    offs = torch.empty((4096, 33), dtype=torch.int32, device=dev)
+    spec = ms.BucketSpec.mod(32)
+    segs = []
+    for i, (st_, n_) in enumerate(zip(starts, sizes)):
+        o = int(st_) * 4
+        segs.append((kall.data_ptr() + o, vall.data_ptr() + o, ko_all.data_ptr() + o, vo_all.data_ptr() + o,
+                     offs[i].data_ptr(), int(n_)))
+    cs = spec.c()
+    stc, plan = ms.ms_batch_plan_create(segs, cs)
+    if stc != ms.MS_OK:
+        raise ms.MsError(stc, "ms_batch_plan_create")
+    sptr = torch.cuda.current_stream().cuda_stream
+    try:
+        t_graph = _time(torch, lambda: ms.ms_batch_run_graph(plan, sptr), reps=5)
+        t_launch = _time(torch, lambda: ms.ms_batch_run(plan, sptr), reps=5)
+
+        def plain():
+            for (kin, vin, kout, vout, off, n_) in segs:
+                st = ms.ms_multisplit_pairs(kin, vin, n_, cs, kout, vout, off, sptr)
+                if st != ms.MS_OK:
+                    raise ms.MsError(st, "plain")
+
+        t_plain = _time(torch, plain, reps=2, warmup=1)
+    finally:
+        ms.ms_batch_plan_destroy(plan)
+    comp = metrics.sol_rate_g(peak, metrics.compulsory_bytes_per_element(True))
+    out["batched_4096_segments_mod32_pairs"] = {
+        "total_pairs": total, "graph_ms": round(t_graph, 3), "launch_ms": round(t_launch, 3),
+        "plain_per_segment_ms": round(t_plain, 3),
+        "gpairs_s_graph": round(metrics.rate_g(total, t_graph * 1e-3), 2),
+        "gpairs_s_plain": round(metrics.rate_g(total, t_plain * 1e-3), 2),
+        "speedup_vs_plain": round(t_plain / t_graph, 2),
+        "frac_compulsory_roofline_graph": round(metrics.rate_g(total, t_graph * 1e-3) / comp, 4)}
+    del kall, vall, ko_all, vo_all, offs
+    torch.cuda.empty_cache()
+
+    # serving: Poisson arrivals of multisplit and sort requests, continuous batching
+    if args.serve_seconds > 0:
+        from paper_1701_01189_gb300 import serving
+
+        out["serving"] = serving.run_config(seconds=args.serve_seconds)
+    if ms.device_status() != ms.MS_OK:
+        raise RuntimeError("device status not OK after the extras")
+    return out
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -434,6 +543,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the radix-sort, batched and serving configurations")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving trace (0: skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -122,6 +122,65 @@ ms_status ms_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, size_t
 ms_status ms_multisplit_keys_noalloc(const uint32_t *keys_in, size_t n, const ms_bucket_spec *spec,
                                      uint32_t *keys_out, uint32_t *offsets, void *stream);
 
+/* ---- Batched multisplit: many independent arrays in one persistent launch.
+ * Not in the paper (it runs one problem per launch); the same method applied
+ * to thousands of uneven arrays at once.  All segments of a plan share one
+ * bucket identifier and are all keys-only (vals_in = vals_out = NULL) or all
+ * key-value.  Each segment's result equals ms_multisplit_keys/_pairs on it. */
+typedef struct {
+  const uint32_t *keys_in;  /* device, n keys */
+  const uint32_t *vals_in;  /* device, n values, or NULL for keys only */
+  uint32_t *keys_out;       /* device, n keys */
+  uint32_t *vals_out;       /* device, n values, or NULL */
+  uint32_t *offsets;        /* device, m+1 bucket starts, or NULL */
+  size_t n;                 /* < 2^32; 0 allowed */
+} ms_segment;
+
+typedef struct ms_batch_plan ms_batch_plan;
+
+/* Reads the host array segs[num_segments] (copied; the device buffers it
+ * names must stay valid while the plan is used, as must spec->splitters) and
+ * builds the work list: one item per 4096-key tile for the tile histograms of
+ * segments longer than one tile, one per tile for the post-scans.  Allocates
+ * the plan's device memory with cudaMalloc and uploads the list
+ * (synchronous; do it once, outside any capture).  Errors:
+ * MS_ERR_INVALID_ARG (bad spec, NULL/overlapping buffers, mixed keys-only and
+ * key-value segments), MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
+ms_status ms_batch_plan_create(const ms_segment *segs, uint32_t num_segments, const ms_bucket_spec *spec,
+                               ms_batch_plan **plan);
+
+/* A plan whose segments change from run to run (for a serving loop): sized
+ * for at most max_segments segments totalling max_elements keys, all keys-only
+ * (pairs = 0) or all key-value (pairs = 1).  Allocates device memory and two
+ * pinned staging areas (synchronous).  Starts with no segments. */
+ms_status ms_batch_plan_create_dynamic(uint32_t max_segments, uint64_t max_elements, int pairs,
+                                       const ms_bucket_spec *spec, ms_batch_plan **plan);
+
+/* Replaces a dynamic plan's segments: validates segs as ms_batch_plan_create
+ * does, builds the work list into a pinned staging area and enqueues its upload
+ * on `stream` (asynchronous; waits only if the staging area's upload of two
+ * calls ago has not finished).  Runs that follow on the same stream use the new
+ * segments; a run must not be in flight on another stream.  Exceeding the
+ * plan's capacity gives MS_ERR_INVALID_ARG. */
+ms_status ms_batch_plan_set_segments(ms_batch_plan *plan, const ms_segment *segs, uint32_t num_segments,
+                                     void *stream);
+
+/* Enqueues on `stream` one memset of the plan's flags and one persistent
+ * kernel that multisplits every segment.  Allocates nothing and does not
+ * synchronize, so it can be captured in a CUDA graph.  Runs of one plan must
+ * not overlap on the GPU (they share the plan's flags and histograms).  Must
+ * be called with the plan's device current. */
+ms_status ms_batch_run(ms_batch_plan *plan, void *stream);
+
+/* The same work, captured into a CUDA graph on the first call (made on a
+ * private stream) and launched on `stream` by every call.  The graph reads the
+ * plan's work list from device memory, so it follows later
+ * ms_batch_plan_set_segments calls. */
+ms_status ms_batch_run_graph(ms_batch_plan *plan, void *stream);
+
+/* Waits for the device, then frees the plan (NULL is fine). */
+ms_status ms_batch_plan_destroy(ms_batch_plan *plan);
+
 /* Reads and clears the calling device's status word: MS_OK, or
  * MS_ERR_TIMEOUT if any bounded device-side wait expired since the last read.
  * Synchronizes `stream` first. */
@@ -154,9 +213,9 @@ ms_status ms_test_expire_lookback(void *stream);
  * n from ms_tune_size_class: 0 below 2^16, 1 below 2^20, 2 below 2^24, 3
  * otherwise).  A variant is: shape of the post-scan tile (0: 8 warps x 16
  * keys per lane, 1: 16 x 8, 2: 8 x 8), rank mode (0: warp ballots, allowed
- * for ceil(log2 m) <= 3; 1: per-warp peer tables) and reorder (1: reorder each
+ * for ceil(log2 m) <= 5; 1: per-warp peer tables) and reorder (1: reorder each
  * tile in shared memory before writing, 0: write from registers; 0 requires
- * rank mode 0).  Unset entries use built-in defaults.  The tuner in
+ * rank mode 0 and ceil(log2 m) <= 3).  Unset entries use built-in defaults.  The tuner in
  * paper_1701_01189_gb300/autotune.py measures the candidates and sets the
  * fastest.  MS_ERR_INVALID_ARG for out-of-range arguments. */
 int ms_tune_size_class(size_t n);

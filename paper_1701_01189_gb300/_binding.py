@@ -33,6 +33,19 @@ _STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_INVALID_ARG", 2: "MS_ERR_UNSUPPORTED", 3
                  4: "MS_ERR_CUDA", 5: "MS_ERR_TIMEOUT"}
 
 
+class _Segment(ctypes.Structure):
+    """ms_segment."""
+
+    _fields_ = [
+        ("keys_in", ctypes.c_void_p),
+        ("vals_in", ctypes.c_void_p),
+        ("keys_out", ctypes.c_void_p),
+        ("vals_out", ctypes.c_void_p),
+        ("offsets", ctypes.c_void_p),
+        ("n", ctypes.c_size_t),
+    ]
+
+
 class _Spec(ctypes.Structure):
     """ms_bucket_spec."""
 
@@ -74,6 +87,16 @@ def lib() -> ctypes.CDLL:
         L.ms_tune_get.argtypes = [I, I, I, I, P, P, P]
         L.ms_tune_reset.argtypes = []
         for f in ("ms_tune_set", "ms_tune_get", "ms_tune_reset"):
+            getattr(L, f).restype = ctypes.c_int
+        L.ms_batch_plan_create.argtypes = [ctypes.POINTER(_Segment), ctypes.c_uint32, SP, ctypes.POINTER(P)]
+        L.ms_batch_plan_create_dynamic.argtypes = [ctypes.c_uint32, ctypes.c_uint64, I, SP, ctypes.POINTER(P)]
+        L.ms_batch_plan_set_segments.argtypes = [P, ctypes.POINTER(_Segment), ctypes.c_uint32, P]
+        L.ms_batch_plan_create_dynamic.restype = ctypes.c_int
+        L.ms_batch_plan_set_segments.restype = ctypes.c_int
+        L.ms_batch_run.argtypes = [P, P]
+        L.ms_batch_run_graph.argtypes = [P, P]
+        L.ms_batch_plan_destroy.argtypes = [P]
+        for f in ("ms_batch_plan_create", "ms_batch_run", "ms_batch_run_graph", "ms_batch_plan_destroy"):
             getattr(L, f).restype = ctypes.c_int
         L.ms_test_expire_lookback.argtypes = [P]
         L.ms_test_expire_lookback.restype = ctypes.c_int
@@ -154,6 +177,43 @@ def ms_status_string(status: int) -> str:
 
 def ms_version() -> str:
     return lib().ms_version().decode()
+
+
+def ms_batch_plan_create(segs, spec: "_Spec"):
+    """segs: list of (keys_in, vals_in, keys_out, vals_out, offsets, n) pointers/sizes.
+    Returns (status, plan handle)."""
+    arr = (_Segment * max(1, len(segs)))()
+    for i, s in enumerate(segs):
+        arr[i] = _Segment(*s)
+    h = ctypes.c_void_p()
+    st = lib().ms_batch_plan_create(arr, len(segs), ctypes.byref(spec), ctypes.byref(h))
+    return st, h
+
+
+def ms_batch_plan_create_dynamic(max_segments: int, max_elements: int, pairs: bool, spec: "_Spec"):
+    h = ctypes.c_void_p()
+    st = lib().ms_batch_plan_create_dynamic(max_segments, max_elements, int(bool(pairs)), ctypes.byref(spec),
+                                            ctypes.byref(h))
+    return st, h
+
+
+def ms_batch_plan_set_segments(plan, segs, stream: int) -> int:
+    arr = (_Segment * max(1, len(segs)))()
+    for i, s in enumerate(segs):
+        arr[i] = _Segment(*s)
+    return lib().ms_batch_plan_set_segments(plan, arr, len(segs), stream)
+
+
+def ms_batch_run(plan, stream: int) -> int:
+    return lib().ms_batch_run(plan, stream)
+
+
+def ms_batch_run_graph(plan, stream: int) -> int:
+    return lib().ms_batch_run_graph(plan, stream)
+
+
+def ms_batch_plan_destroy(plan) -> int:
+    return lib().ms_batch_plan_destroy(plan)
 
 
 # ----------------------------------------------------------------- torch-tensor helpers
@@ -270,6 +330,49 @@ def radix_sort(keys, vals=None, begin_bit: int = 0, end_bit: int = 32, keys_out=
     _check(ms_radix_sort(keys.data_ptr(), vptr, n, begin_bit, end_bit, keys_out.data_ptr(), voptr,
                          _stream(stream)), "ms_radix_sort")
     return keys_out, (vals_out if vals is not None else None)
+
+
+class BatchPlan:
+    """A batched multisplit over many CUDA tensors (torch) with one bucket spec.
+
+    ``keys`` / ``vals`` are lists of 1-D 32-bit CUDA tensors (vals may be None);
+    outputs and offsets are allocated here.  ``run()`` enqueues one persistent
+    launch; ``run(graph=True)`` replays it from a CUDA graph.
+    """
+
+    def __init__(self, keys, vals, spec: BucketSpec):
+        import torch
+
+        self.spec = spec
+        self.keys = [_u32_view(k) for k in keys]
+        self.vals = None if vals is None else [_u32_view(v) for v in vals]
+        self.keys_out = [torch.empty_like(k) for k in self.keys]
+        self.vals_out = None if vals is None else [torch.empty_like(v) for v in self.vals]
+        dev = self.keys[0].device if self.keys else torch.device("cuda")
+        self.offsets = [torch.empty(spec.m + 1, dtype=torch.int32, device=dev) for _ in self.keys]
+        segs = []
+        for i, k in enumerate(self.keys):
+            segs.append((k.data_ptr(), None if vals is None else self.vals[i].data_ptr(),
+                         self.keys_out[i].data_ptr(), None if vals is None else self.vals_out[i].data_ptr(),
+                         self.offsets[i].data_ptr(), k.numel()))
+        self._cspec = spec.c()
+        st, self.handle = ms_batch_plan_create(segs, self._cspec)
+        _check(st, "ms_batch_plan_create")
+
+    def run(self, graph: bool = False, stream=None):
+        f = ms_batch_run_graph if graph else ms_batch_run
+        _check(f(self.handle, _stream(stream)), "ms_batch_run")
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            ms_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def device_status(stream=None) -> int:

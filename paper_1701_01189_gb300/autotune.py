@@ -25,8 +25,10 @@ def variants(log2m: int):
     out = []
     for shape in (0, 1, 2):
         out.append((shape, 1, 1))
+        if log2m <= 5:
+            out.append((shape, 0, 1))
         if log2m <= 3:
-            out += [(shape, 0, 1), (shape, 0, 0)]
+            out.append((shape, 0, 0))
     return out
 
 

@@ -56,6 +56,8 @@ static ms_status current_ctx(DeviceCtx** out) {
   return MS_OK;
 }
 
+ms_status current_device_ctx(DeviceCtx** out) { return current_ctx(out); }
+
 cudaError_t scratch_alloc(DeviceCtx& ctx, void** p, size_t bytes, cudaStream_t stream) {
   return cudaMallocFromPoolAsync(p, bytes ? bytes : 16, ctx.pool, stream);
 }
@@ -227,6 +229,10 @@ extern "C" ms_status ms_radix_sort(const uint32_t* keys_in, const uint32_t* vals
     if (e == cudaSuccess && pairs) e = cudaMemcpyAsync(vals_out, vals_in, bytes, cudaMemcpyDeviceToDevice, s);
     return to_status(e);
   }
+  if (n < ((size_t)1 << 30))
+    return to_status(run_onesweep_sort(keys_in, pairs ? vals_in : nullptr, (uint32_t)n, begin_bit, end_bit, keys_out,
+                                       pairs ? vals_out : nullptr, s, *ctx));
+  // n >= 2^30: one three-stage multisplit per digit
   const int passes = (width + 7) / 8;
   void* tmp = nullptr;
   uint32_t* tmp_k = nullptr;

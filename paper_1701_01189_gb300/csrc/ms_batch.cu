@@ -1,0 +1,539 @@
+// ms_batch.cu -- many independent multisplits in one persistent launch.
+//
+// Not in the paper (which sizes one problem per launch); this is the batching
+// form of the same method for many small and uneven arrays, where launching
+// the three stages once per array is dominated by launch latency (cf. the
+// small-frontier overhead the paper notes for SSSP, Section 7.2).
+//
+// A plan flattens every segment into a list of tile work items, in two
+// groups: (A) the histogram of each tile of every segment that spans more than
+// one tile, and (B) the post-scan of every tile of every segment, where a
+// segment of a single tile is done in one item from start to finish (its own
+// tile histogram is the whole H, so no global scan is needed).  CTAs of one
+// persistent grid take items in ticket order.  The CTA that finishes the last
+// histogram of a segment scans that segment's histogram matrix (bucket-major,
+// one column per tile: Eq. 2 with the segment's tiles as subproblems) and
+// raises the segment's ready flag; post-scan items of the segment wait for
+// that flag (bounded).  Every item a CTA waits for has an earlier ticket, so
+// it belongs to a CTA that is already running: the waits always end.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ms.h"
+#include "ms_host.h"
+#include "ms_kernels.cuh"
+#include "ms_scan.cuh"
+
+struct ms_batch_plan;  // defined below (outside the namespace, as declared in ms.h)
+
+namespace ms {
+
+constexpr int kBatchNW = 8, kBatchItems = 16;
+constexpr uint32_t kBatchTile = kBatchNW * 32 * kBatchItems;  // 4096
+
+struct DevSeg {
+  const uint32_t* kin;
+  const uint32_t* vin;
+  uint32_t* kout;
+  uint32_t* vout;
+  uint32_t* offsets;  // m+1 words or nullptr
+  uint32_t n;
+  uint32_t L;         // tiles
+  uint32_t hoff;      // first word of the segment's H in the plan's pool (multi-tile only)
+  uint32_t pad;
+};
+
+struct BatchArgs {
+  const DevSeg* segs;
+  const uint2* items;    // items[0] = (n_hist, n_items); then (segment, tile) pairs, histograms first
+  uint32_t* H;           // histogram pool
+  uint32_t* done;        // per segment: histogram items finished (zeroed per run)
+  uint32_t* ready;       // per segment: scan finished (zeroed per run)
+  uint32_t* ticket;      // zeroed per run
+  uint32_t* err;
+  DevSpec sp;
+};
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Shared memory (words): splitter table 256, LUT, s_base 256, s_delta 256,
+// s_warp 32, counters NW*257, peer tables 2*NW*256, tile keys T, tile values T
+// (pairs), reorder keys T, values T (pairs), bucket bytes T.
+template <int KIND, bool PAIRS>
+struct BatchLayout {
+  static constexpr uint32_t T = kBatchTile;
+  static __host__ __device__ uint32_t lut() { return 256; }
+  static __host__ __device__ uint32_t base(uint32_t lb) { return lut() + lut_words<KIND>(lb); }
+  static __host__ __device__ uint32_t cnt(uint32_t lb) { return base(lb) + 256 + 256 + 32; }
+  static __host__ __device__ uint32_t peer(uint32_t lb) { return cnt(lb) + kBatchNW * 257; }
+  static __host__ __device__ uint32_t tile(uint32_t lb) { return (peer(lb) + 2 * kBatchNW * 256 + 3) & ~3u; }
+  static __host__ __device__ uint32_t reorder(uint32_t lb) { return tile(lb) + T * (PAIRS ? 2 : 1); }
+  static __host__ size_t bytes(uint32_t lb) { return 4u * (size_t)(reorder(lb) + T * (PAIRS ? 2 : 1)) + T; }
+};
+
+template <int KIND, bool PAIRS>
+__global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArgs a) {
+  using Lay = BatchLayout<KIND, PAIRS>;
+  constexpr uint32_t T = Lay::T;
+  constexpr int THREADS = kBatchNW * 32;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_item, s_flag;
+  const DevSpec& sp = a.sp;
+  const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1, lb = sp.lut_bits;
+  uint32_t* s_tbl = smem;
+  uint2* s_lut = reinterpret_cast<uint2*>(smem + Lay::lut());
+  uint32_t* s_base = smem + Lay::base(lb);
+  uint32_t* s_delta = s_base + 256;
+  uint32_t* s_warp = s_delta + 256;
+  uint32_t* s_cnt = smem + Lay::cnt(lb);
+  uint32_t* s_peer = smem + Lay::peer(lb);
+  uint32_t* t_keys = smem + Lay::tile(lb);
+  uint32_t* t_vals = t_keys + T;
+  uint32_t* s_keys = smem + Lay::reorder(lb);
+  uint32_t* s_vals = s_keys + T;
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + T * (PAIRS ? 2 : 1));
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  uint32_t* wc = s_cnt + w * S;
+  uint32_t* wpeer = s_peer + w * 2 * m_pad;
+  const uint32_t off0 = w * (32 * kBatchItems) + lane;
+  const uint32_t lane_x[1] = {0u};
+
+  for (uint32_t i = threadIdx.x; i < 2 * kBatchNW * m_pad; i += THREADS) s_peer[i] = 0u;
+  build_bucket_tables<KIND, 8>(sp, s_tbl, s_lut);  // ends with a barrier
+  const uint2 counts = a.items[0];  // read from memory so a captured graph follows later updates
+  const uint32_t n_hist = counts.x, n_items = counts.y;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= n_items) break;
+    const uint2 item = a.items[1 + it];
+    const DevSeg sg = a.segs[item.x];
+    const uint32_t tile = item.y;
+    const size_t tbase = (size_t)tile * T;
+    const uint32_t tile_n = (uint32_t)min((size_t)T, (size_t)sg.n - tbase);
+
+    // the tile's keys (and values) into shared memory
+    for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
+      t_keys[p] = __ldcs(sg.kin + tbase + p);
+      if constexpr (PAIRS)
+        if (it >= n_hist) t_vals[p] = __ldcs(sg.vin + tbase + p);
+    }
+    __syncthreads();
+    const uint32_t avail = tile_n - min(tile_n, w * (32u * kBatchItems));
+    uint32_t rb[kBatchItems];
+    if (tile_n == T)
+      rank_windows<KIND, 8, kBatchItems, kRankTable, true>(t_keys + off0, avail, sp, s_tbl, s_lut, wc, wpeer, m_pad,
+                                                          m, lane_x, lanemask_lt(), lane, rb);
+    else
+      rank_windows<KIND, 8, kBatchItems, kRankTable, false>(t_keys + off0, avail, sp, s_tbl, s_lut, wc, wpeer,
+                                                           m_pad, m, lane_x, lanemask_lt(), lane, rb);
+    __syncthreads();
+    const uint32_t total = scan_tile_counters<kBatchNW>(s_cnt, S, m_pad, s_warp);
+
+    if (it < n_hist) {
+      // (A) tile histogram -> column `tile` of the segment's H
+      if (threadIdx.x < m) {
+        const uint32_t b = threadIdx.x;
+        const uint32_t hist = ((b + 1 < m_pad) ? s_cnt[b + 1] : total) - s_cnt[b];
+        a.H[sg.hoff + b * sg.L + tile] = hist;
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_flag = (atomicAdd(a.done + item.x, 1u) == sg.L - 1) ? 1u : 0u;
+      __syncthreads();
+      if (s_flag) {
+        // last histogram of the segment: exclusive scan of its H (m*L words,
+        // bucket-major), bucket offsets, then the ready flag
+        __threadfence();
+        const uint32_t len = m * sg.L;
+        uint32_t* Hs = a.H + sg.hoff;
+        uint32_t carry = 0;
+        for (uint32_t base = 0; base < len; base += THREADS) {
+          const uint32_t e = base + threadIdx.x;
+          const uint32_t v = e < len ? __ldcg(Hs + e) : 0u;
+          uint32_t tot;
+          const uint32_t ex = block_exclusive_scan<kBatchNW>(v, s_warp, &tot);
+          if (e < len) {
+            Hs[e] = carry + ex;
+            if (sg.offsets != nullptr && e % sg.L == 0u) sg.offsets[e / sg.L] = carry + ex;
+          }
+          carry += tot;
+        }
+        if (sg.offsets != nullptr && threadIdx.x == 0) sg.offsets[m] = carry;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release_u32(a.ready + item.x, 1u);
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // (B) post-scan of one tile: global base of each bucket for this tile
+    if (sg.L == 1) {
+      if (threadIdx.x < m) s_base[threadIdx.x] = s_cnt[threadIdx.x];  // the tile is the segment
+      if (sg.offsets != nullptr) {
+        if (threadIdx.x < m) sg.offsets[threadIdx.x] = s_cnt[threadIdx.x];
+        if (threadIdx.x == 0) sg.offsets[m] = total;
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        uint32_t spins = 0;
+        while (ld_acquire_u32(a.ready + item.x) == 0u) {
+          // give up at the bound, or at once when another wait has already given up
+          if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
+            atomicOr(a.err, kDevErrTimeout);
+            break;
+          }
+          __nanosleep(spins < 64 ? 64 : 512);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < m) s_base[threadIdx.x] = __ldcg(a.H + sg.hoff + threadIdx.x * sg.L + tile);
+    }
+    if (threadIdx.x < m) s_delta[threadIdx.x] = s_base[threadIdx.x] - s_cnt[threadIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kBatchItems; ++i) {
+      if (off0 + i * 32 < tile_n) {
+        const uint32_t b = rb[i] >> 16;
+        const uint32_t p = wc[b] + (rb[i] & 0xffffu);
+        if (p < T) {
+          s_keys[p] = t_keys[off0 + i * 32];
+          if constexpr (PAIRS) s_vals[p] = t_vals[off0 + i * 32];
+          s_bkt[p] = (uint8_t)b;
+        } else {
+          atomicOr(a.err, kDevErrBounds);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kBatchItems; ++k) {
+      const uint32_t p = threadIdx.x + k * THREADS;
+      if (p < tile_n) {
+        const uint32_t g = s_delta[s_bkt[p]] + p;
+        if (g < sg.n) {
+          __stcs(sg.kout + g, s_keys[p]);
+          if constexpr (PAIRS) __stcs(sg.vout + g, s_vals[p]);
+        } else {
+          atomicOr(a.err, kDevErrBounds);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace ms
+
+using namespace ms;
+
+struct ms_batch_plan {
+  int device = -1;
+  int kind = 0;
+  bool pairs = false;
+  DevSpec sp;
+  // capacities (fixed at creation) and the current work
+  uint32_t max_segments = 0, max_items = 0;
+  uint64_t max_hwords = 0;
+  uint32_t num_segments = 0, n_items = 0;
+  uint32_t grid = 0;
+  size_t smem = 0;
+  DevSeg* d_segs = nullptr;
+  uint2* d_items = nullptr;  // [0] = (n_hist, n_items), then the items
+  uint32_t* d_H = nullptr;
+  uint32_t* d_flags = nullptr;  // done[max_segments] | ready[max_segments] | ticket
+  size_t flags_bytes = 0;
+  uint32_t* d_err = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  // dynamic plans: two pinned staging areas for segment tables and items
+  void* h_stage[2] = {nullptr, nullptr};
+  cudaEvent_t stage_done[2] = {nullptr, nullptr};
+  int stage_next = 0;
+};
+
+namespace ms {
+
+template <int KIND, bool PAIRS>
+static cudaError_t batch_setup(ms_batch_plan& p, int sm_count) {
+  auto k = k_batch<KIND, PAIRS>;
+  p.smem = BatchLayout<KIND, PAIRS>::bytes(p.sp.lut_bits);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  int nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBatchNW * 32, p.smem);
+  if (e != cudaSuccess) return e;
+  p.grid = (uint32_t)std::max(1, nb) * (uint32_t)sm_count;
+  return cudaSuccess;
+}
+
+template <int KIND, bool PAIRS>
+static cudaError_t batch_launch(const ms_batch_plan& p, cudaStream_t s) {
+  BatchArgs a;
+  a.segs = p.d_segs;
+  a.items = p.d_items;
+  a.H = p.d_H;
+  a.done = p.d_flags;
+  a.ready = p.d_flags + p.max_segments;
+  a.ticket = p.d_flags + 2 * p.max_segments;
+  a.err = p.d_err;
+  a.sp = p.sp;
+  k_batch<KIND, PAIRS><<<p.grid, kBatchNW * 32, p.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int KIND>
+static cudaError_t batch_dispatch(ms_batch_plan& p, int sm_count, cudaStream_t s, bool setup) {
+  if (p.pairs) return setup ? batch_setup<KIND, true>(p, sm_count) : batch_launch<KIND, true>(p, s);
+  return setup ? batch_setup<KIND, false>(p, sm_count) : batch_launch<KIND, false>(p, s);
+}
+
+static cudaError_t batch_call(ms_batch_plan& p, int sm_count, cudaStream_t s, bool setup) {
+  switch (p.kind) {
+    case kRange: return batch_dispatch<kRange>(p, sm_count, s, setup);
+    case kDelta: return batch_dispatch<kDelta>(p, sm_count, s, setup);
+    case kRadix: return batch_dispatch<kRadix>(p, sm_count, s, setup);
+    default: return batch_dispatch<kMod>(p, sm_count, s, setup);
+  }
+}
+
+static void plan_free(ms_batch_plan* p) {
+  if (p == nullptr) return;
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (int k = 0; k < 2; ++k) {
+    if (p->stage_done[k]) cudaEventDestroy(p->stage_done[k]);
+    if (p->h_stage[k]) cudaFreeHost(p->h_stage[k]);
+  }
+  cudaFree(p->d_segs);
+  cudaFree(p->d_items);
+  cudaFree(p->d_H);
+  cudaFree(p->d_flags);
+  delete p;
+}
+
+}  // namespace ms
+
+namespace ms {
+
+// Validates segs and builds the segment table and the work list (histogram
+// items first).  Returns the histogram words needed in *hwords.
+static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec& sp, bool pairs, DevSeg* hs,
+                            std::vector<uint2>& items, uint64_t* hwords) {
+  std::vector<uint2> post;
+  items.clear();
+  items.push_back(make_uint2(0u, 0u));  // counts, filled below
+  uint64_t hw = 0;
+  for (uint32_t i = 0; i < num; ++i) {
+    const ms_segment& g = segs[i];
+    if (g.n >= ((size_t)1 << 32)) return MS_ERR_INVALID_ARG;
+    if ((g.vals_in != nullptr) != pairs || (g.vals_out != nullptr) != pairs) return MS_ERR_INVALID_ARG;
+    const size_t bytes = g.n * 4;
+    if (g.n > 0 && (g.keys_in == nullptr || g.keys_out == nullptr || overlap(g.keys_in, g.keys_out, bytes)))
+      return MS_ERR_INVALID_ARG;
+    if (pairs && g.n > 0 &&
+        (overlap(g.vals_in, g.vals_out, bytes) || overlap(g.vals_out, g.keys_out, bytes) ||
+         overlap(g.vals_out, g.keys_in, bytes) || overlap(g.keys_out, g.vals_in, bytes)))
+      return MS_ERR_INVALID_ARG;
+    DevSeg d;
+    std::memset(&d, 0, sizeof d);
+    d.kin = g.keys_in;
+    d.vin = g.vals_in;
+    d.kout = g.keys_out;
+    d.vout = g.vals_out;
+    d.offsets = g.offsets;
+    d.n = (uint32_t)g.n;
+    // an empty segment still gets one (empty) item: it writes zero offsets
+    d.L = std::max<uint32_t>(1u, (uint32_t)((g.n + kBatchTile - 1) / kBatchTile));
+    if (d.L > 1) {
+      d.hoff = (uint32_t)hw;
+      hw += (uint64_t)sp.m * d.L;
+      for (uint32_t t = 0; t < d.L; ++t) items.push_back(make_uint2(i, t));
+    }
+    for (uint32_t t = 0; t < d.L; ++t) post.push_back(make_uint2(i, t));
+    hs[i] = d;
+  }
+  const uint32_t n_hist = (uint32_t)(items.size() - 1);
+  items.insert(items.end(), post.begin(), post.end());
+  items[0] = make_uint2(n_hist, (uint32_t)(items.size() - 1));
+  if (hw >= ((uint64_t)1 << 32)) return MS_ERR_UNSUPPORTED;
+  *hwords = hw;
+  return MS_OK;
+}
+
+// Allocates a plan's device memory for the given capacities.
+static ms_status plan_alloc(ms_batch_plan* p, DeviceCtx* ctx, int kind, bool pairs, const DevSpec& sp,
+                            uint32_t max_segments, uint32_t max_items, uint64_t max_hwords) {
+  p->device = ctx->device;
+  p->kind = kind;
+  p->pairs = pairs;
+  p->sp = sp;
+  p->d_err = ctx->d_err;
+  p->max_segments = max_segments;
+  p->max_items = max_items;
+  p->max_hwords = max_hwords;
+  p->flags_bytes = ((size_t)2 * max_segments + 4) * 4;
+  cudaError_t e = cudaMalloc(&p->d_segs, std::max<size_t>(1, max_segments) * sizeof(DevSeg));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_items, ((size_t)max_items + 1) * sizeof(uint2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_H, std::max<uint64_t>(1, max_hwords) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_flags, p->flags_bytes);
+  if (e == cudaSuccess) e = cudaMemset(p->d_items, 0, sizeof(uint2));
+  if (e == cudaSuccess) e = batch_call(*p, ctx->sm_count, nullptr, true);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MS_ERR_OUT_OF_MEMORY : MS_ERR_CUDA;
+  }
+  return MS_OK;
+}
+
+}  // namespace ms
+
+extern "C" ms_status ms_batch_plan_create(const ms_segment* segs, uint32_t num_segments, const ms_bucket_spec* spec,
+                                          ms_batch_plan** plan) {
+  if (plan == nullptr) return MS_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (num_segments > 0 && segs == nullptr) return MS_ERR_INVALID_ARG;
+  DevSpec sp;
+  int kind = 0;
+  ms_status st = make_devspec(spec, &sp, &kind);
+  if (st != MS_OK) return st;
+  const bool pairs = num_segments > 0 && segs[0].vals_in != nullptr;
+  std::vector<DevSeg> hs(num_segments);
+  std::vector<uint2> items;
+  uint64_t hwords = 0;
+  st = build_work(segs, num_segments, sp, pairs, hs.data(), items, &hwords);
+  if (st != MS_OK) return st;
+  DeviceCtx* ctx = nullptr;
+  st = current_device_ctx(&ctx);
+  if (st != MS_OK) return st;
+  auto* p = new ms_batch_plan();
+  st = plan_alloc(p, ctx, kind, pairs, sp, num_segments, (uint32_t)(items.size() - 1), hwords);
+  p->num_segments = num_segments;
+  p->n_items = items[0].y;
+  cudaError_t e = cudaSuccess;
+  if (st == MS_OK && !hs.empty())
+    e = cudaMemcpy(p->d_segs, hs.data(), hs.size() * sizeof(DevSeg), cudaMemcpyHostToDevice);
+  if (st == MS_OK && e == cudaSuccess)
+    e = cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+  if (st == MS_OK && e != cudaSuccess) st = to_status(e);
+  if (st != MS_OK) {
+    plan_free(p);
+    return st;
+  }
+  *plan = p;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_batch_plan_create_dynamic(uint32_t max_segments, uint64_t max_elements, int pairs,
+                                                  const ms_bucket_spec* spec, ms_batch_plan** plan) {
+  if (plan == nullptr) return MS_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (max_segments == 0) return MS_ERR_INVALID_ARG;
+  DevSpec sp;
+  int kind = 0;
+  ms_status st = make_devspec(spec, &sp, &kind);
+  if (st != MS_OK) return st;
+  // every segment adds at most one partial tile
+  const uint64_t tiles = max_elements / kBatchTile + max_segments;
+  if (2 * tiles >= ((uint64_t)1 << 31)) return MS_ERR_INVALID_ARG;
+  DeviceCtx* ctx = nullptr;
+  st = current_device_ctx(&ctx);
+  if (st != MS_OK) return st;
+  auto* p = new ms_batch_plan();
+  st = plan_alloc(p, ctx, kind, pairs != 0, sp, max_segments, (uint32_t)(2 * tiles), (uint64_t)sp.m * tiles);
+  const size_t stage_bytes = (size_t)max_segments * sizeof(DevSeg) + ((size_t)2 * tiles + 1) * sizeof(uint2);
+  for (int k = 0; k < 2 && st == MS_OK; ++k) {
+    if (cudaMallocHost(&p->h_stage[k], stage_bytes) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->stage_done[k], cudaEventDisableTiming) != cudaSuccess)
+      st = MS_ERR_OUT_OF_MEMORY;
+  }
+  if (st != MS_OK) {
+    cudaGetLastError();
+    plan_free(p);
+    return st;
+  }
+  *plan = p;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_batch_plan_set_segments(ms_batch_plan* plan, const ms_segment* segs, uint32_t num_segments,
+                                                void* stream) {
+  if (plan == nullptr || plan->h_stage[0] == nullptr) return MS_ERR_INVALID_ARG;
+  if (num_segments > plan->max_segments || (num_segments > 0 && segs == nullptr)) return MS_ERR_INVALID_ARG;
+  const int k = plan->stage_next;
+  // the staging area is free once its previous upload has been read
+  if (cudaEventSynchronize(plan->stage_done[k]) != cudaSuccess) return MS_ERR_CUDA;
+  DevSeg* hs = static_cast<DevSeg*>(plan->h_stage[k]);
+  std::vector<uint2> items;
+  uint64_t hwords = 0;
+  ms_status st = build_work(segs, num_segments, plan->sp, plan->pairs, hs, items, &hwords);
+  if (st != MS_OK) return st;
+  if (items.size() - 1 > plan->max_items || hwords > plan->max_hwords) return MS_ERR_INVALID_ARG;
+  uint2* hi = reinterpret_cast<uint2*>(static_cast<char*>(plan->h_stage[k]) +
+                                       (size_t)plan->max_segments * sizeof(DevSeg));
+  std::memcpy(hi, items.data(), items.size() * sizeof(uint2));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (num_segments > 0) e = cudaMemcpyAsync(plan->d_segs, hs, num_segments * sizeof(DevSeg), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(plan->d_items, hi, items.size() * sizeof(uint2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(plan->stage_done[k], s);
+  if (e != cudaSuccess) return to_status(e);
+  plan->num_segments = num_segments;
+  plan->n_items = items[0].y;
+  plan->stage_next = k ^ 1;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_batch_run(ms_batch_plan* plan, void* stream) {
+  if (plan == nullptr) return MS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MS_ERR_CUDA;
+  if (dev != plan->device) return MS_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(plan->d_flags, 0, plan->flags_bytes, s);
+  if (e == cudaSuccess) e = batch_call(*plan, 0, s, false);
+  return to_status(e);
+}
+
+extern "C" ms_status ms_batch_run_graph(ms_batch_plan* plan, void* stream) {
+  if (plan == nullptr) return MS_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (plan->graph == nullptr) {
+    // capture the memset and the launch once, on a private stream
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MS_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    ms_status st = MS_OK;
+    if (e == cudaSuccess) {
+      st = ms_batch_run(plan, cs);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess && st == MS_OK) e = cudaGraphInstantiate(&plan->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (st != MS_OK) return st;
+    if (e != cudaSuccess) return to_status(e);
+  }
+  return to_status(cudaGraphLaunch(plan->graph, s));
+}
+
+extern "C" ms_status ms_batch_plan_destroy(ms_batch_plan* plan) {
+  if (plan == nullptr) return MS_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+  }
+  plan_free(plan);
+  return MS_OK;
+}

@@ -68,6 +68,12 @@ namespace ms {
 ms_status to_status(cudaError_t e);
 ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kind);
 bool overlap(const void* a, const void* b, size_t bytes);
+// The calling device's state, created on first use (allocates: not inside a capture).
+ms_status current_device_ctx(DeviceCtx** out);
+
+// LSD radix sort with one sweep per digit (ms_onesweep.cu); n < 2^30.
+cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t n, int begin_bit, int end_bit,
+                              uint32_t* keys_out, uint32_t* vals_out, cudaStream_t s, DeviceCtx& ctx);
 
 // Scratch from the library pool, ordered on `stream`.
 cudaError_t scratch_alloc(DeviceCtx& ctx, void** p, size_t bytes, cudaStream_t stream);

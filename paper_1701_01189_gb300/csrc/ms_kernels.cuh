@@ -28,7 +28,10 @@
 //    ballots give, at a cost that does not grow with log m).
 #pragma once
 
+#include <type_traits>
+
 #include "ms_bucket.cuh"
+#include "ms_tma.cuh"
 
 namespace ms {
 
@@ -159,41 +162,193 @@ __host__ size_t prescan_smem_bytes(uint32_t m_pad, uint32_t lut_bits) {
   return 4u * (256u + lut_words<KIND>(lut_bits) + NW * m_pad * 9u);
 }
 
+// Ranks the ITEMS windows of one warp (Section 5.5: a direct solve per
+// 32-key window).  wk points at this lane's first key (the warp's keys are
+// wk[i*32] for window i); `avail` is the number of keys of the warp's share
+// counted from its first key (only read when !FULL).  On return rb[i] holds
+// the key's rank among the earlier keys of its bucket in this warp (low 16
+// bits) and the bucket (bits 16..23), and wc[b] (table mode) or wc[lane]
+// (ballot mode) the warp's count of bucket b.
+template <int KIND, int NB, int ITEMS, int RANK, bool FULL>
+__device__ __forceinline__ void rank_windows(const uint32_t* wk, uint32_t avail, const DevSpec& sp,
+                                             const uint32_t* s_tbl, const uint2* s_lut, uint32_t* wc,
+                                             uint32_t* wpeer, uint32_t m_pad, uint32_t m, const uint32_t* lane_x,
+                                             uint32_t lt_mask, uint32_t lane, uint32_t (&rb)[ITEMS]) {
+  if constexpr (RANK == kRankTable) {
+    for (uint32_t b = lane; b < m_pad; b += 32) wc[b] = 0u;
+    __syncwarp();
+  }
+  uint32_t run = 0;  // ballot mode: keys of bucket `lane` in earlier windows of this warp
+  (void)run;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const bool valid = FULL || (uint32_t)(i * 32) + lane < avail;
+    const uint32_t b = valid ? bucket_of<KIND, NB>(wk[i * 32], sp, s_tbl, s_lut) : 0u;
+    if constexpr (RANK == kRankBallot) {
+      // Section 5.4 / Alg. 2 / Alg. 3: NB ballots give every lane the bucket
+      // of every lane of the window.
+      const uint32_t vb = FULL ? kFull : __ballot_sync(kFull, valid);
+      uint32_t own = vb, lane_bm = vb;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const uint32_t bal = __ballot_sync(kFull, (b >> k) & 1u);
+        own &= ((b >> k) & 1u) ? bal : ~bal;
+        lane_bm &= bal ^ lane_x[k];
+      }
+      const uint32_t before = __shfl_sync(kFull, run, b & 31u);
+      rb[i] = (before + __popc(own & lt_mask)) | (b << 16);
+      run += __popc(lane_bm);
+    } else {
+      // peer table (two, alternating by window): OR the lane bit into the
+      // bucket's entry, read the peers back; the lowest peer advances the
+      // warp's counter of the bucket and clears the entry.
+      uint32_t* tb = wpeer + (i & 1) * m_pad;
+      if (valid) atomicOr(tb + b, 1u << lane);
+      __syncwarp();
+      const uint32_t own = valid ? tb[b] : 0u;
+      __syncwarp();
+      const uint32_t lt = own & lt_mask;
+      uint32_t before = 0;
+      if (valid && lt == 0u) {
+        before = atomicAdd(wc + b, (uint32_t)__popc(own));
+        tb[b] = 0u;
+      }
+      before = __shfl_sync(kFull, before, (__ffs(own) - 1) & 31);
+      rb[i] = (before + __popc(lt)) | (b << 16);
+    }
+  }
+  if constexpr (RANK == kRankBallot) wc[lane] = (lane < m) ? run : 0u;
+}
+
+// One exclusive scan over the per-warp bucket counters s_cnt[w*S + b] in
+// bucket-major order, in place: afterwards s_cnt[w*S + b] is where warp w's
+// keys of bucket b start in the reordered tile -- earlier buckets of the tile
+// (Section 5.6.2, item 2) plus earlier warps of the same bucket (Section
+// 5.5.4, third term).  Returns the tile's key count.  All threads call it;
+// it contains block barriers and ends with one.
+template <int NW>
+__device__ __forceinline__ uint32_t scan_tile_counters(uint32_t* s_cnt, uint32_t S, uint32_t m_pad, uint32_t* s_warp) {
+  constexpr int LOGNW = NW == 8 ? 3 : NW == 16 ? 4 : 5;
+  const uint32_t ept = m_pad >> 5;  // entries per thread (1..8)
+  uint32_t pre[8];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if ((uint32_t)k < ept) {
+      const uint32_t e = threadIdx.x * ept + k;
+      const uint32_t v = s_cnt[(e & (NW - 1)) * S + (e >> LOGNW)];
+      pre[k] = sum;
+      sum += v;
+    }
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<NW>(sum, s_warp, &total);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if ((uint32_t)k < ept) {
+      const uint32_t e = threadIdx.x * ept + k;
+      s_cnt[(e & (NW - 1)) * S + (e >> LOGNW)] = excl + pre[k];
+    }
+  }
+  __syncthreads();
+  return total;
+}
+
 // ---------------------------------------------------------------------------
-// Post-scan.  Dynamic shared memory (words): splitter table (256), LUT,
-// s_run / s_delta (256 each), s_warp (32), counters NW*(m_pad+1), two peer
-// tables per warp 2*NW*m_pad (table mode), then (block reorder) the reorder
-// buffers: T keys, T values (pairs), T bucket bytes.
+// Post-scan.
+//
+// Each CTA walks the tiles of its chunk.  Full tiles arrive by bulk
+// asynchronous copies (TMA) into a ring of STAGES shared-memory slots, issued
+// by one thread STAGES tiles ahead and completed on one mbarrier per slot, so
+// HBM latency overlaps the work on earlier tiles; the partial last tile (and
+// every tile when the inputs are not 16-byte aligned) is copied in by the
+// threads themselves.  Keys are read from the slot twice (ranking, then the
+// scatter), so they do not occupy registers in between.
 //
 // REORDER = 1: the block-level reordering of Section 5.6.2 (writes coalesced
-// per bucket run).  REORDER = 0: each key goes straight from its registers to
-// its final position (the no-reorder design of Section 5.3's DMS), which for
-// a few buckets already gives runs of consecutive addresses per warp store.
-template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int MINB>
+// per bucket run).  REORDER = 0: each key goes from its slot straight to its
+// final position (the no-reorder design of Section 5.3's DMS), which for a
+// few buckets already gives runs of consecutive addresses per warp store.
+//
+// Dynamic shared memory, in order: STAGES mbarriers (64 bytes), the ring
+// (STAGES*T keys, STAGES*T values), splitter table (256 words), LUT, s_run,
+// s_delta (256 words each), s_warp (32), counters NW*(m_pad+1), two peer
+// tables per warp (table mode), and with REORDER the reorder buffers (T keys,
+// T values, T bucket bytes).
+template <int KIND, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int STAGES>
+struct PostLayout {
+  static constexpr uint32_t T = NW * 32 * ITEMS;
+  static constexpr uint32_t kRing = 16;  // words: after the mbarriers
+  static constexpr uint32_t kRingWords = STAGES * T * (PAIRS ? 2 : 1);
+  static __host__ __device__ uint32_t tbl() { return kRing + kRingWords; }
+  static __host__ __device__ uint32_t lut() { return tbl() + 256; }
+  static __host__ __device__ uint32_t run(uint32_t lb) { return lut() + lut_words<KIND>(lb); }
+  static __host__ __device__ uint32_t cnt(uint32_t lb) { return run(lb) + 256 + 256 + 32; }
+  static __host__ __device__ uint32_t peer(uint32_t lb, uint32_t m_pad) { return cnt(lb) + NW * (m_pad + 1); }
+  static __host__ __device__ uint32_t reorder(uint32_t lb, uint32_t m_pad) {
+    return (peer(lb, m_pad) + (RANK == kRankTable ? 2 * NW * m_pad : 0u) + 3u) & ~3u;
+  }
+  static __host__ size_t bytes(uint32_t m_pad, uint32_t lb) {
+    return 4u * (size_t)(reorder(lb, m_pad) + (REORDER ? T * (PAIRS ? 2u : 1u) : 0u)) + (REORDER ? T : 0u);
+  }
+};
+
+template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int MINB, int STAGES>
 __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
+  using Lay = PostLayout<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>;
   constexpr int THREADS = NW * 32;
-  constexpr int T = THREADS * ITEMS;
+  constexpr uint32_t T = Lay::T;
   static_assert(NW >= 8, "the per-bucket phase needs >= 256 threads");
   static_assert(NW == 8 || NW == 16 || NW == 32, "NW must be 8, 16 or 32");
   static_assert(RANK == kRankTable || NB <= 5, "ballot ranks need m <= 32");
+  static_assert(STAGES >= 1 && STAGES <= 4, "1..4 ring slots");
   constexpr int LOGNW = NW == 8 ? 3 : NW == 16 ? 4 : 5;
   extern __shared__ __align__(16) uint32_t smem[];
   const DevSpec& sp = a.sp;
-  const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1;
-  uint32_t* s_tbl = smem;
-  uint2* s_lut = reinterpret_cast<uint2*>(smem + 256);
-  uint32_t* s_run = smem + 256 + lut_words<KIND>(sp.lut_bits);
+  const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1, lb = sp.lut_bits;
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* ring_k = smem + Lay::kRing;
+  uint32_t* ring_v = ring_k + STAGES * T;  // pairs
+  uint32_t* s_tbl = smem + Lay::tbl();
+  uint2* s_lut = reinterpret_cast<uint2*>(smem + Lay::lut());
+  uint32_t* s_run = smem + Lay::run(lb);
   uint32_t* s_delta = s_run + 256;
   uint32_t* s_warp = s_delta + 256;
-  uint32_t* s_cnt = s_warp + 32;                                           // [w * S + b]
-  uint32_t* s_peer = s_cnt + NW * S;                                       // [w][2][m_pad]
-  uint32_t* s_keys = s_peer + (RANK == kRankTable ? 2 * NW * m_pad : 0u);  // T
-  uint32_t* s_vals = s_keys + T;                                           // T (pairs)
+  uint32_t* s_cnt = smem + Lay::cnt(lb);           // [w * S + b]
+  uint32_t* s_peer = smem + Lay::peer(lb, m_pad);  // [w][2][m_pad]
+  uint32_t* s_keys = smem + Lay::reorder(lb, m_pad);
+  uint32_t* s_vals = s_keys + T;
   uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + T * (PAIRS ? 2 : 1));
+  __shared__ uint32_t s_pend[STAGES];  // 1 + index of the tile whose copy is in flight in the slot, 0 if none
 
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   const uint32_t c = blockIdx.x;
   const uint32_t len = m * a.G;
+  const uint32_t t0 = c * a.tiles_per_cta;
+  const uint32_t t1 = min(t0 + a.tiles_per_cta, a.num_tiles);
+  const uint32_t ntiles = t1 > t0 ? t1 - t0 : 0u;
+  auto tile_of = [&](uint32_t j) { return a.reverse ? t1 - 1 - j : t0 + j; };
+  auto is_full = [&](uint32_t j) { return (size_t)(tile_of(j) + 1) * T <= a.n; };
+  const bool use_tma = a.prefetch != 0u;  // inputs 16-byte aligned
+
+  // thread 0: start the copy of this CTA's tile j into its ring slot
+  auto issue = [&](uint32_t j) {
+    if (!use_tma || j >= ntiles || !is_full(j)) return;
+    const uint32_t slot = j % STAGES;
+    const size_t base = (size_t)tile_of(j) * T;
+    mbar_arrive_expect_tx(s_bar + slot, T * 4u * (PAIRS ? 2u : 1u));
+    bulk_g2s(ring_k + slot * T, a.keys_in + base, T * 4u, s_bar + slot);
+    if constexpr (PAIRS) bulk_g2s(ring_v + slot * T, a.vals_in + base, T * 4u, s_bar + slot);
+    s_pend[slot] = j + 1;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < STAGES; ++k) {
+      mbar_init(s_bar + k, 1);
+      s_pend[k] = 0;
+    }
+    fence_mbar_init();
+  }
   if (RANK == kRankTable)
     for (uint32_t i = threadIdx.x; i < 2 * NW * m_pad; i += THREADS) s_peer[i] = 0u;
   // next global position of each bucket: chunk start (forward) or chunk end (reverse)
@@ -201,6 +356,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
     const uint32_t e = b * a.G + c;
     s_run[b] = a.reverse ? ((e + 1 < len) ? a.Gx[e + 1] : a.n) : a.Gx[e];
   }
+  __syncthreads();  // mbarriers initialised
+  if (threadIdx.x == 0)
+    for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);
   build_bucket_tables<KIND, NB>(sp, s_tbl, s_lut);  // ends with a barrier
 
   uint32_t* wc = s_cnt + w * S;
@@ -211,102 +369,40 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   uint32_t lane_x[NB > 0 ? NB : 1];
 #pragma unroll
   for (int k = 0; k < NB; ++k) lane_x[k] = ((lane >> k) & 1u) ? 0u : 0xffffffffu;
+  const uint32_t off0 = w * (32 * ITEMS) + lane;
+  // bit k: parity of the next completion of slot k's mbarrier (a slot filled
+  // by plain loads for a partial tile does not advance its barrier)
+  uint32_t phase = 0;
 
-  const uint32_t t0 = c * a.tiles_per_cta;
-  const uint32_t t1 = min(t0 + a.tiles_per_cta, a.num_tiles);
-  const uint32_t ntiles = t1 > t0 ? t1 - t0 : 0u;
-  for (uint32_t j = 0; j < ntiles; ++j) {
-    const uint32_t tile = a.reverse ? t1 - 1 - j : t0 + j;
-    if (a.prefetch && threadIdx.x == 0 && j + 2 < ntiles) {
-      const uint32_t pt = a.reverse ? t1 - 3 - j : t0 + j + 2;
-      if ((size_t)(pt + 1) * T <= a.n) {  // a full tile only
-        prefetch_l2(a.keys_in + (size_t)pt * T, T * 4u);
-        if constexpr (PAIRS) prefetch_l2(a.vals_in + (size_t)pt * T, T * 4u);
-      }
-    }
+  // One tile.  FULL: all T keys present (no per-key bounds tests).
+  auto tile_body = [&](auto full_tag, uint32_t j) -> bool {
+    constexpr bool FULL = decltype(full_tag)::value;
+    const uint32_t tile = tile_of(j);
     const size_t tbase = (size_t)tile * T;
-    const uint32_t tile_n = (uint32_t)min((size_t)T, (size_t)a.n - tbase);
-    const uint32_t off0 = w * (32 * ITEMS) + lane;
-    const uint32_t* ksrc = a.keys_in + tbase;
-    const uint32_t* vsrc = PAIRS ? a.vals_in + tbase : nullptr;
-    uint32_t key[ITEMS], val[ITEMS], rb[ITEMS];  // rb: rank in warp (low 16 bits) | bucket << 16
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const bool valid = off0 + i * 32 < tile_n;
-      key[i] = valid ? __ldcs(ksrc + off0 + i * 32) : 0u;
-      if constexpr (PAIRS) val[i] = valid ? __ldcs(vsrc + off0 + i * 32) : 0u;
-    }
-    if constexpr (RANK == kRankTable) {
-      for (uint32_t b = lane; b < m_pad; b += 32) wc[b] = 0u;
-      __syncwarp();
-    }
-    uint32_t run = 0;  // ballot mode: keys of bucket `lane` in earlier windows of this warp
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const bool valid = off0 + i * 32 < tile_n;
-      const uint32_t b = valid ? bucket_of<KIND, NB>(key[i], sp, s_tbl, s_lut) : 0u;
-      if constexpr (RANK == kRankBallot) {
-        // Section 5.4 / Alg. 2 / Alg. 3: NB ballots give every lane the
-        // bucket of every lane of the window.
-        const uint32_t vb = __ballot_sync(kFull, valid);
-        uint32_t own = vb, lane_bm = vb;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-          const uint32_t bal = __ballot_sync(kFull, (b >> k) & 1u);
-          own &= ((b >> k) & 1u) ? bal : ~bal;
-          lane_bm &= bal ^ lane_x[k];
-        }
-        const uint32_t before = __shfl_sync(kFull, run, b & 31u);
-        rb[i] = (before + __popc(own & lt_mask)) | (b << 16);
-        run += __popc(lane_bm);
-      } else {
-        // peer table (two, alternating by window): OR the lane bit into the
-        // bucket's entry, read the peers back; the lowest peer advances the
-        // warp's counter of the bucket and clears the entry.
-        uint32_t* tbl = wpeer + (i & 1) * m_pad;
-        if (valid) atomicOr(tbl + b, 1u << lane);
-        __syncwarp();
-        const uint32_t own = valid ? tbl[b] : 0u;
-        __syncwarp();
-        const uint32_t lt = own & lt_mask;
-        uint32_t before = 0;
-        if (valid && lt == 0u) {
-          before = atomicAdd(wc + b, (uint32_t)__popc(own));
-          tbl[b] = 0u;
-        }
-        before = __shfl_sync(kFull, before, (__ffs(own) - 1) & 31);
-        rb[i] = (before + __popc(lt)) | (b << 16);
+    const uint32_t tile_n = FULL ? T : (uint32_t)((size_t)a.n - tbase);
+    const uint32_t slot = j % STAGES;
+    const uint32_t* rk = ring_k + slot * T;
+    const uint32_t* rv = ring_v + slot * T;
+    (void)rv;
+    bool ok = true;
+    if (FULL && use_tma) {
+      ok = mbar_wait(s_bar + slot, (phase >> slot) & 1u, a.err);
+      phase ^= 1u << slot;
+    } else {
+      // copy the tile into the slot with plain loads (no copy is in flight there)
+      for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
+        ring_k[slot * T + p] = __ldcs(a.keys_in + tbase + p);
+        if constexpr (PAIRS) ring_v[slot * T + p] = __ldcs(a.vals_in + tbase + p);
       }
+      __syncthreads();
     }
-    if constexpr (RANK == kRankBallot) wc[lane] = (lane < m) ? run : 0u;
-    __syncthreads();
+    uint32_t rb[ITEMS];  // rank in warp (low 16 bits) | bucket << 16
+    rank_windows<KIND, NB, ITEMS, RANK, FULL>(rk + off0, tile_n - min(tile_n, off0 - lane), sp, s_tbl, s_lut, wc,
+                                              wpeer, m_pad, m, lane_x, lt_mask, lane, rb);
+    if (__syncthreads_or(!ok)) return false;
 
-    // One exclusive scan over the (bucket, warp) counters in bucket-major
-    // order gives, for every warp and bucket, where its keys start in the
-    // reordered tile: earlier buckets of the tile (Section 5.6.2, item 2) plus
-    // earlier warps of the same bucket (Section 5.5.4, third term).
-    const uint32_t ept = m_pad >> 5;  // entries per thread (1..8)
-    uint32_t pre[8];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if ((uint32_t)k < ept) {
-        const uint32_t e = threadIdx.x * ept + k;
-        const uint32_t v = s_cnt[(e & (NW - 1)) * S + (e >> LOGNW)];
-        pre[k] = sum;
-        sum += v;
-      }
-    }
-    uint32_t total;
-    const uint32_t excl = block_exclusive_scan<NW>(sum, s_warp, &total);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if ((uint32_t)k < ept) {
-        const uint32_t e = threadIdx.x * ept + k;
-        s_cnt[(e & (NW - 1)) * S + (e >> LOGNW)] = excl + pre[k];
-      }
-    }
-    __syncthreads();
+    // where each (bucket, warp) starts in the reordered tile
+    const uint32_t total = scan_tile_counters<NW>(s_cnt, S, m_pad, s_warp);
 
     // Per bucket: global position minus tile position.
     if (threadIdx.x < m) {
@@ -327,12 +423,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
       // Reorder the tile (a local stable multisplit of Section 4.7).
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
-        if (off0 + i * 32 < tile_n) {
+        if (FULL || off0 + i * 32 < tile_n) {
           const uint32_t b = rb[i] >> 16;
           const uint32_t p = wc[b] + (rb[i] & 0xffffu);
-          if (p < (uint32_t)T) {
-            s_keys[p] = key[i];
-            if constexpr (PAIRS) s_vals[p] = val[i];
+          if (p < T) {
+            s_keys[p] = rk[off0 + i * 32];
+            if constexpr (PAIRS) s_vals[p] = rv[off0 + i * 32];
             s_bkt[p] = (uint8_t)b;
           } else {
             atomicOr(a.err, kDevErrBounds);
@@ -340,44 +436,69 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
         }
       }
       __syncthreads();
+      // the slot is free again: start the copy of the tile STAGES ahead
+      if (threadIdx.x == 0) {
+        s_pend[slot] = 0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(j + STAGES);
+      }
       // Consecutive threads hold consecutive keys of one bucket run: the
       // global writes are coalesced per run.
-#pragma unroll 4
-      for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
-        const uint32_t g = s_delta[s_bkt[p]] + p;
-        if (g < a.n) {
-          __stcs(a.keys_out + g, s_keys[p]);
-          if constexpr (PAIRS) __stcs(a.vals_out + g, s_vals[p]);
-        } else {
-          atomicOr(a.err, kDevErrBounds);
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const uint32_t p = threadIdx.x + k * THREADS;
+        if (FULL || p < tile_n) {
+          const uint32_t g = s_delta[s_bkt[p]] + p;
+          if (g < a.n) {
+            __stcs(a.keys_out + g, s_keys[p]);
+            if constexpr (PAIRS) __stcs(a.vals_out + g, s_vals[p]);
+          } else {
+            atomicOr(a.err, kDevErrBounds);
+          }
         }
       }
     } else {
       __syncthreads();  // s_delta ready
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
-        if (off0 + i * 32 < tile_n) {
+        if (FULL || off0 + i * 32 < tile_n) {
           const uint32_t b = rb[i] >> 16;
           const uint32_t g = s_delta[b] + wc[b] + (rb[i] & 0xffffu);
           if (g < a.n) {
-            __stcs(a.keys_out + g, key[i]);
-            if constexpr (PAIRS) __stcs(a.vals_out + g, val[i]);
+            __stcs(a.keys_out + g, rk[off0 + i * 32]);
+            if constexpr (PAIRS) __stcs(a.vals_out + g, rv[off0 + i * 32]);
           } else {
             atomicOr(a.err, kDevErrBounds);
           }
         }
       }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_pend[slot] = 0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(j + STAGES);
+      }
     }
     __syncthreads();
+    return true;
+  };
+
+  for (uint32_t j = 0; j < ntiles; ++j) {
+    const bool ok = is_full(j) ? tile_body(std::true_type{}, j) : tile_body(std::false_type{}, j);
+    if (!ok) {
+      // a copy never completed: wait (bounded) for the copies still in flight, then stop
+      if (threadIdx.x == 0)
+        for (int k = 0; k < STAGES; ++k)
+          if (s_pend[k] != 0u) mbar_wait(s_bar + k, (phase >> k) & 1u, a.err);
+      __syncthreads();
+      return;
+    }
   }
 }
 
-template <int KIND, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER>
+template <int KIND, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int STAGES>
 __host__ size_t postscan_smem_bytes(uint32_t m_pad, uint32_t lut_bits) {
-  constexpr uint32_t T = NW * 32 * ITEMS;
-  return 4u * (256u + lut_words<KIND>(lut_bits) + 256u + 256u + 32u + NW * (m_pad + 1u) +
-               (RANK == kRankTable ? 2 * NW * m_pad : 0u) + (REORDER ? T * (PAIRS ? 2u : 1u) : 0u)) +
-         (REORDER ? T : 0u);
+  return PostLayout<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>::bytes(m_pad, lut_bits);
 }
 
 }  // namespace ms

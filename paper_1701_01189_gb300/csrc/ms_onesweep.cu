@@ -1,0 +1,353 @@
+// ms_onesweep.cu -- the LSD radix sort of Section 7.1 with one sweep per digit.
+//
+// Section 7.1 builds the sort from ceil(32/r) multisplits with the radix digit
+// f_k(u) = (u >> kr) & (2^r - 1) as bucket identifier; each of those is the
+// three-stage multisplit (pre-scan, scan, post-scan), reading the keys twice
+// per digit.  On GB300 the per-digit pre-scan is replaced as in the
+// "single-sweep" LSD sorts (Adinets and Merrill, "Onesweep", 2022): one kernel
+// reads the keys once and counts the digits of every pass (the first term of
+// Eq. 2 for every pass, since a histogram does not depend on the order of the
+// keys), and each pass is then a single kernel whose tiles obtain the second
+// term of Eq. 2 -- the count of their digit in all earlier tiles -- by a
+// decoupled look-back over per-tile, per-digit status words, instead of a
+// separate scan of a histogram matrix.  The ranking, the scan over (digit,
+// warp) counters and the reordered, coalesced writes are the multisplit's own
+// (ms_kernels.cuh).  Result: 4 + 8 bytes per key per pass instead of 12.
+//
+// Status words are 32-bit: bits 31..30 a flag (1: tile aggregate, 2:
+// inclusive prefix), bits 29..0 a count, so this path takes n < 2^30.  Two
+// status arrays alternate between passes; every tile clears its words of the
+// array the next pass will use.  All waits are bounded.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "ms.h"
+#include "ms_host.h"
+#include "ms_kernels.cuh"
+#include "ms_scan.cuh"
+
+namespace ms {
+
+constexpr uint32_t kOsAggregate = 1u << 30;
+constexpr uint32_t kOsPrefix = 2u << 30;
+constexpr uint32_t kOsValue = (1u << 30) - 1u;
+constexpr int kOsNW = 8, kOsItems = 16;
+constexpr uint32_t kOsTile = kOsNW * 32 * kOsItems;  // 4096 keys
+constexpr int kHistNW = 8, kHistItems = 16;
+
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+struct RadixHistArgs {
+  const uint32_t* keys;
+  uint32_t n;
+  uint32_t begin_bit, end_bit, passes;
+  uint32_t* hist;  // passes * 256, zeroed
+};
+
+// Digit histograms of every pass in one read of the keys.  Per warp, 32-bit
+// counters [pass][digit] in shared memory; at the end the CTA adds its counts
+// into the global histograms.
+__global__ void __launch_bounds__(kHistNW * 32) k_radix_hist(RadixHistArgs a) {
+  constexpr uint32_t T = kHistNW * 32 * kHistItems;
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  uint32_t* wh = smem + w * 4 * 256;
+  for (uint32_t i = threadIdx.x; i < kHistNW * 4 * 256; i += kHistNW * 32) smem[i] = 0u;
+  __syncthreads();
+  for (size_t tb = (size_t)blockIdx.x * T; tb < a.n; tb += (size_t)gridDim.x * T) {
+    const uint32_t rem = (uint32_t)min((size_t)T, (size_t)a.n - tb);
+    const uint32_t off0 = w * (32 * kHistItems) + lane;
+    uint32_t key[kHistItems];
+#pragma unroll
+    for (int i = 0; i < kHistItems; ++i) key[i] = (off0 + i * 32 < rem) ? a.keys[tb + off0 + i * 32] : 0u;
+#pragma unroll
+    for (int i = 0; i < kHistItems; ++i) {
+      if (off0 + i * 32 < rem) {
+        for (uint32_t p = 0; p < a.passes; ++p) {
+          const uint32_t sh = a.begin_bit + 8 * p;
+          const uint32_t bits = min(8u, a.end_bit - sh);
+          atomicAdd(wh + p * 256 + ((key[i] >> sh) & ((1u << bits) - 1u)), 1u);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < a.passes * 256; i += kHistNW * 32) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int ww = 0; ww < kHistNW; ++ww) s += smem[ww * 4 * 256 + i];
+    if (s) atomicAdd(a.hist + i, s);
+  }
+}
+
+struct OnesweepArgs {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  uint32_t n;
+  DevSpec sp;              // radix digit of this pass (kRadix)
+  const uint32_t* hist;    // this pass's digit histogram (m entries)
+  uint32_t* status;        // this pass: num_tiles * 256 words, zero
+  uint32_t* status_next;   // the next pass's array: cleared here
+  uint32_t* ticket;        // zero
+  uint32_t* err;
+  uint32_t aligned;        // inputs 16-byte aligned: full tiles arrive by TMA
+};
+
+// Shared memory (words): mbarrier (16), slot keys T, slot values T (pairs),
+// s_goff 256, s_delta 256, s_warp 32, s_cnt NW*257, s_peer 2*NW*256, reorder
+// keys T, values T (pairs), bucket bytes T.
+template <bool PAIRS>
+struct OsLayout {
+  static constexpr uint32_t T = kOsTile;
+  static constexpr uint32_t kSlot = 16;
+  static constexpr uint32_t kGoff = kSlot + T * (PAIRS ? 2 : 1);
+  static constexpr uint32_t kDelta = kGoff + 256;
+  static constexpr uint32_t kWarp = kDelta + 256;
+  static constexpr uint32_t kCnt = kWarp + 32;
+  static constexpr uint32_t kPeer = kCnt + kOsNW * 257;
+  static constexpr uint32_t kReorder = (kPeer + 2 * kOsNW * 256 + 3) & ~3u;
+  static constexpr size_t kBytes = 4u * (size_t)(kReorder + T * (PAIRS ? 2 : 1)) + T;
+};
+
+template <bool PAIRS>
+__global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(OnesweepArgs a) {
+  using Lay = OsLayout<PAIRS>;
+  constexpr uint32_t T = Lay::T;
+  constexpr int THREADS = kOsNW * 32;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_tile_id;
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* slot_k = smem + Lay::kSlot;
+  uint32_t* slot_v = slot_k + T;
+  uint32_t* s_goff = smem + Lay::kGoff;
+  uint32_t* s_delta = smem + Lay::kDelta;
+  uint32_t* s_warp = smem + Lay::kWarp;
+  uint32_t* s_cnt = smem + Lay::kCnt;
+  uint32_t* s_peer = smem + Lay::kPeer;
+  uint32_t* s_keys = smem + Lay::kReorder;
+  uint32_t* s_vals = s_keys + T;
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + T * (PAIRS ? 2 : 1));
+  const DevSpec& sp = a.sp;
+  const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1;
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+
+  // Tiles are numbered by ticket, so every earlier tile belongs to a CTA that
+  // already started: the look-back below always makes progress.
+  if (threadIdx.x == 0) {
+    const uint32_t tile = atomicAdd(a.ticket, 1u);
+    s_tile_id = tile;
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+    const size_t tbase = (size_t)tile * T;
+    if (a.aligned && tbase + T <= a.n) {
+      mbar_arrive_expect_tx(s_bar, T * 4u * (PAIRS ? 2u : 1u));
+      bulk_g2s(slot_k, a.keys_in + tbase, T * 4u, s_bar);
+      if constexpr (PAIRS) bulk_g2s(slot_v, a.vals_in + tbase, T * 4u, s_bar);
+    }
+  }
+  __syncthreads();
+  const uint32_t tile = s_tile_id;
+  const size_t tbase = (size_t)tile * T;
+  const uint32_t tile_n = (uint32_t)min((size_t)T, (size_t)a.n - tbase);
+  const bool tma = a.aligned && tile_n == T;
+
+  // digit offsets of this pass (first term of Eq. 2): exclusive scan of the histogram
+  {
+    const uint32_t v = threadIdx.x < m ? a.hist[threadIdx.x] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<kOsNW>(v, s_warp, &tot);
+    if (threadIdx.x < m) s_goff[threadIdx.x] = ex;
+  }
+  for (uint32_t i = threadIdx.x; i < 2 * kOsNW * m_pad; i += THREADS) s_peer[i] = 0u;
+  if (a.status_next != nullptr)
+    for (uint32_t d = threadIdx.x; d < 256; d += THREADS) a.status_next[(size_t)tile * 256 + d] = 0u;
+  bool ok = true;
+  if (tma) {
+    ok = mbar_wait(s_bar, 0, a.err);
+  } else {
+    for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
+      slot_k[p] = __ldcs(a.keys_in + tbase + p);
+      if constexpr (PAIRS) slot_v[p] = __ldcs(a.vals_in + tbase + p);
+    }
+  }
+  __syncthreads();
+
+  uint32_t* wc = s_cnt + w * S;
+  uint32_t* wpeer = s_peer + w * 2 * m_pad;
+  const uint32_t off0 = w * (32 * kOsItems) + lane;
+  const uint32_t avail = tile_n - min(tile_n, w * (32u * kOsItems));
+  uint32_t rb[kOsItems];
+  const uint32_t lane_x[1] = {0u};
+  if (tile_n == T)
+    rank_windows<kRadix, 8, kOsItems, kRankTable, true>(slot_k + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad,
+                                                       m, lane_x, lanemask_lt(), lane, rb);
+  else
+    rank_windows<kRadix, 8, kOsItems, kRankTable, false>(slot_k + off0, avail, sp, nullptr, nullptr, wc, wpeer,
+                                                        m_pad, m, lane_x, lanemask_lt(), lane, rb);
+  if (__syncthreads_or(!ok)) return;  // a copy never arrived (the error bit is set)
+  const uint32_t total = scan_tile_counters<kOsNW>(s_cnt, S, m_pad, s_warp);
+
+  // Decoupled look-back per digit: publish this tile's count, add up the
+  // earlier tiles' counts until one carries an inclusive prefix.
+  if (threadIdx.x < m) {
+    const uint32_t d = threadIdx.x;
+    const uint32_t tstart = s_cnt[d];
+    const uint32_t hist = ((d + 1 < m_pad) ? s_cnt[d + 1] : total) - tstart;
+    uint32_t* st = a.status + (size_t)tile * 256 + d;
+    uint32_t excl = 0;
+    if (tile == 0) {
+      st_relaxed_u32(st, kOsPrefix | hist);
+    } else {
+      st_relaxed_u32(st, kOsAggregate | hist);
+      for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
+        const uint32_t* q = a.status + (size_t)p * 256 + d;
+        uint32_t v = ld_relaxed_u32(q);
+        uint32_t spins = 0;
+        while ((v & ~kOsValue) == 0u) {
+          // give up at the bound, or at once when another wait has already given up
+          if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
+            atomicOr(a.err, kDevErrTimeout);
+            v = kOsPrefix;
+            break;
+          }
+          __nanosleep(spins < 64 ? 32 : 256);
+          v = ld_relaxed_u32(q);
+        }
+        excl += v & kOsValue;
+        if ((v & ~kOsValue) == kOsPrefix) break;
+      }
+      st_relaxed_u32(st, kOsPrefix | ((excl + hist) & kOsValue));
+    }
+    s_delta[d] = s_goff[d] + excl - tstart;
+  }
+  __syncthreads();
+
+  // reorder the tile by digit in shared memory, then coalesced writes
+#pragma unroll
+  for (int i = 0; i < kOsItems; ++i) {
+    if (off0 + i * 32 < tile_n) {
+      const uint32_t b = rb[i] >> 16;
+      const uint32_t p = wc[b] + (rb[i] & 0xffffu);
+      if (p < T) {
+        s_keys[p] = slot_k[off0 + i * 32];
+        if constexpr (PAIRS) s_vals[p] = slot_v[off0 + i * 32];
+        s_bkt[p] = (uint8_t)b;
+      } else {
+        atomicOr(a.err, kDevErrBounds);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kOsItems; ++k) {
+    const uint32_t p = threadIdx.x + k * THREADS;
+    if (p < tile_n) {
+      const uint32_t g = s_delta[s_bkt[p]] + p;
+      if (g < a.n) {
+        __stcs(a.keys_out + g, s_keys[p]);
+        if constexpr (PAIRS) __stcs(a.vals_out + g, s_vals[p]);
+      } else {
+        atomicOr(a.err, kDevErrBounds);
+      }
+    }
+  }
+}
+
+// Whole sort on `stream`: 2 <= passes, n < 2^30.  Scratch from the pool:
+// histograms, two status arrays, tickets, one ping-pong buffer per array.
+cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t n, int begin_bit, int end_bit,
+                              uint32_t* keys_out, uint32_t* vals_out, cudaStream_t s, DeviceCtx& ctx) {
+  const bool pairs = vals_in != nullptr;
+  const uint32_t passes = (uint32_t)((end_bit - begin_bit + 7) / 8);
+  const uint32_t L = (n + kOsTile - 1) / kOsTile;
+  const size_t hist_b = 4u * 256u * 4u;
+  const size_t status_b = (size_t)L * 256u * 4u;
+  const size_t tick_b = 64;
+  const size_t buf_b = passes > 1 ? (size_t)n * 4u * (pairs ? 2u : 1u) : 0u;
+  const size_t buf_off = (hist_b + 2 * status_b + tick_b + 255) & ~(size_t)255;
+  void* ws = nullptr;
+  cudaError_t e = scratch_alloc(ctx, &ws, buf_off + buf_b, s);
+  if (e != cudaSuccess) return e;
+  char* base = static_cast<char*>(ws);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base);
+  uint32_t* status[2] = {reinterpret_cast<uint32_t*>(base + hist_b),
+                         reinterpret_cast<uint32_t*>(base + hist_b + status_b)};
+  uint32_t* tickets = reinterpret_cast<uint32_t*>(base + hist_b + 2 * status_b);
+  uint32_t* tmp_k = reinterpret_cast<uint32_t*>(base + buf_off);
+  uint32_t* tmp_v = pairs ? tmp_k + n : nullptr;
+  e = cudaMemsetAsync(ws, 0, hist_b + 2 * status_b + tick_b, s);
+
+  {
+    // dynamic shared memory opt-in, once per device
+    static std::mutex mu;
+    static uint64_t ready = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    const int d = ctx.device & 63;
+    if (!((ready >> d) & 1ull)) {
+      cudaFuncSetAttribute(k_radix_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, kHistNW * 4 * 256 * 4);
+      cudaFuncSetAttribute(k_onesweep_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)OsLayout<false>::kBytes);
+      cudaFuncSetAttribute(k_onesweep_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)OsLayout<true>::kBytes);
+      ready |= 1ull << d;
+    }
+  }
+  if (e == cudaSuccess) {
+    RadixHistArgs ha{keys_in, n, (uint32_t)begin_bit, (uint32_t)end_bit, passes, hist};
+    const uint32_t grid = std::min<uint32_t>((n + kHistNW * 32 * kHistItems - 1) / (kHistNW * 32 * kHistItems),
+                                             (uint32_t)ctx.sm_count * 4u);
+    k_radix_hist<<<std::max(grid, 1u), kHistNW * 32, kHistNW * 4 * 256 * 4, s>>>(ha);
+    e = cudaGetLastError();
+  }
+  const uint32_t aligned = ((reinterpret_cast<uintptr_t>(keys_in) | reinterpret_cast<uintptr_t>(vals_in) |
+                             reinterpret_cast<uintptr_t>(keys_out) | reinterpret_cast<uintptr_t>(vals_out) |
+                             reinterpret_cast<uintptr_t>(tmp_k) | reinterpret_cast<uintptr_t>(tmp_v)) & 15u) == 0;
+  const uint32_t* src_k = keys_in;
+  const uint32_t* src_v = vals_in;
+  for (uint32_t p = 0; p < passes && e == cudaSuccess; ++p) {
+    const uint32_t shift = (uint32_t)begin_bit + 8 * p;
+    const uint32_t bits = std::min(8u, (uint32_t)end_bit - shift);
+    const bool to_out = ((passes - 1 - p) % 2) == 0;
+    uint32_t* dst_k = to_out ? keys_out : tmp_k;
+    uint32_t* dst_v = to_out ? vals_out : tmp_v;
+    OnesweepArgs oa;
+    std::memset(&oa, 0, sizeof oa);
+    oa.keys_in = src_k;
+    oa.vals_in = pairs ? src_v : nullptr;
+    oa.keys_out = dst_k;
+    oa.vals_out = pairs ? dst_v : nullptr;
+    oa.n = n;
+    oa.sp.m = 1u << bits;
+    oa.sp.nbits = bits;
+    oa.sp.shift = shift;
+    oa.sp.mask = (1u << bits) - 1u;
+    oa.sp.m_pad = oa.sp.m <= 32 ? 32u : oa.sp.m;
+    oa.hist = hist + p * 256;
+    oa.status = status[p & 1];
+    oa.status_next = (p + 1 < passes) ? status[(p + 1) & 1] : nullptr;
+    oa.ticket = tickets + p;
+    oa.err = ctx.d_err;
+    oa.aligned = aligned;
+    if (pairs)
+      k_onesweep_pass<true><<<L, kOsNW * 32, OsLayout<true>::kBytes, s>>>(oa);
+    else
+      k_onesweep_pass<false><<<L, kOsNW * 32, OsLayout<false>::kBytes, s>>>(oa);
+    e = cudaGetLastError();
+    src_k = dst_k;
+    src_v = dst_v;
+  }
+  const cudaError_t e2 = scratch_free(ws, s);
+  return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace ms

@@ -56,19 +56,19 @@ static inline Chunking make_chunking(uint32_t n, uint32_t T, uint32_t max_ctas) 
 // search of range buckets; 8 covers every m.
 constexpr int kPreNW = 8, kPreItems = 16, kPreMinB = 3;
 
-template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int MINB>
+template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int MINB, int STAGES = 2>
 static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   constexpr int THREADS = NW * 32;
   constexpr uint32_t T = THREADS * ITEMS;
   constexpr int NBPRE = KIND == kRange ? 8 : 0;
   auto kpre = k_prescan<KIND, NBPRE, kPreNW, kPreItems, kPreMinB>;
-  auto kpost = k_postscan<KIND, NB, NW, ITEMS, PAIRS, RANK, REORDER, MINB>;
+  auto kpost = k_postscan<KIND, NB, NW, ITEMS, PAIRS, RANK, REORDER, MINB, STAGES>;
   const uint32_t m_pad = c.sp.m_pad, lb = c.sp.lut_bits;
   const uint32_t mp_max = RANK == kRankBallot ? 32u : 256u;
   const size_t smem_pre_max = prescan_smem_bytes<KIND, kPreNW>(256, 11);
-  const size_t smem_post_max = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER>(mp_max, 11);
+  const size_t smem_post_max = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>(mp_max, 11);
   const size_t smem_pre = prescan_smem_bytes<KIND, kPreNW>(m_pad, lb);
-  const size_t smem_post = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER>(m_pad, lb);
+  const size_t smem_post = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>(m_pad, lb);
   static LaunchInfo li_pre, li_post;
   const int nb_post = setup_kernel(li_post, kpost, THREADS, smem_post_max, smem_post, ctx.device);
   const int nb_pre = setup_kernel(li_pre, kpre, kPreNW * 32, smem_pre_max, smem_pre, ctx.device);
@@ -143,21 +143,24 @@ static cudaError_t run_ms_pairs(const Call& c, DeviceCtx& ctx, int shape) {
 
 template <int KIND, int NB>
 static cudaError_t run_ms_ballot(const Call& c, DeviceCtx& ctx, const Variant& v) {
-  if (v.reorder) return run_ms_pairs<KIND, NB, kRankBallot, 1>(c, ctx, v.shape);
-  return run_ms_pairs<KIND, NB, kRankBallot, 0>(c, ctx, v.shape);
+  if (v.reorder || NB > 3) return run_ms_pairs<KIND, NB, kRankBallot, 1>(c, ctx, v.shape);
+  return run_ms_pairs<KIND, (NB > 3 ? 3 : NB), kRankBallot, 0>(c, ctx, v.shape);
 }
 
-// Ballot ranks are built for m <= 8 (NB <= 3); every m runs with peer tables
-// (NB = 8 sizes the range-splitter search for any m).
+// Ballot ranks are built for m <= 32 (NB <= 5; direct writes only for m <= 8);
+// every m runs with peer tables (NB = 8 sizes the range-splitter search for
+// any m).
 template <int KIND>
 static cudaError_t run_ms_kind(const Call& c, DeviceCtx& ctx) {
   const Variant v = choose_variant(c);
-  if (v.rank == kRankBallot && c.sp.nbits <= 3) {
+  if (v.rank == kRankBallot && c.sp.nbits <= 5) {
     switch (c.sp.nbits) {
       case 0: return run_ms_ballot<KIND, 0>(c, ctx, v);
       case 1: return run_ms_ballot<KIND, 1>(c, ctx, v);
       case 2: return run_ms_ballot<KIND, 2>(c, ctx, v);
-      default: return run_ms_ballot<KIND, 3>(c, ctx, v);
+      case 3: return run_ms_ballot<KIND, 3>(c, ctx, v);
+      case 4: return run_ms_ballot<KIND, 4>(c, ctx, v);
+      default: return run_ms_ballot<KIND, 5>(c, ctx, v);
     }
   }
   return run_ms_pairs<KIND, 8, kRankTable, 1>(c, ctx, v.shape);

@@ -41,7 +41,8 @@ __device__ __forceinline__ unsigned long long wait_status(const unsigned long lo
   unsigned long long v = ld_relaxed_u64(p);
   uint32_t spins = 0;
   while ((v >> 32) == 0) {
-    if (++spins > kSpinLimit) {
+    // give up at the bound, or at once when another wait has already given up
+    if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)err & kDevErrTimeout))) {
       atomicOr(err, kDevErrTimeout);
       return kFlagPrefix;  // value 0, treated as a prefix: stop looking back
     }

@@ -74,12 +74,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// Bounded wait for phase `phase` of `bar`.  Returns false (and sets the
-// timeout bit of *err) if the limit is reached.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for phase `phase` of `bar`.  try_wait may itself suspend the
+// thread for a while, so the bound is on elapsed time (about one second,
+// read from the global nanosecond timer) as well as on the iteration count.
+// Returns false (and sets the timeout bit of *err) when the bound is reached.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t* err) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const uint64_t t0 = global_ns();
   for (uint32_t i = 0; i < kMbarSpinLimit; ++i) {
     if (mbar_try_wait(bar, phase)) return true;
-    if (i > 64) __nanosleep(64);
+    if ((i & 63u) == 63u && (global_ns() - t0 > 1000000000ull || (*(volatile uint32_t*)err & kDevErrTimeout))) break;
   }
   atomicOr(err, kDevErrTimeout);
   return false;

@@ -16,11 +16,21 @@ std::mutex g_mu;
 bool g_set[kKinds][2][kNbits][kClasses] = {};
 Variant g_table[kKinds][2][kNbits][kClasses];
 
-Variant default_variant(int nbits) {
+// Measured on GB300 at n = 2^26 (all four identifiers): up to 8 buckets, warp
+// ballots with writes straight from registers win; beyond, peer tables with
+// block reordering.  Key-value pairs prefer the smaller 8 x 8 tile (two
+// arrays in flight per tile), except with 256 buckets (16 x 8).
+Variant default_variant(int nbits, int pairs) {
   Variant v;
-  v.shape = 0;
-  v.rank = nbits <= 2 ? kRankBallot : kRankTable;  // ballots are cheap for up to 4 buckets
-  v.reorder = nbits == 0 ? 0 : 1;                  // one bucket: a plain copy, already coalesced
+  if (nbits <= 3) {
+    v.rank = kRankBallot;
+    v.reorder = 0;
+    v.shape = pairs ? 2 : 0;
+  } else {
+    v.rank = kRankTable;
+    v.reorder = 1;
+    v.shape = pairs ? (nbits >= 8 ? 1 : 2) : 0;
+  }
   return v;
 }
 }  // namespace
@@ -36,7 +46,7 @@ Variant choose_variant(const Call& c) {
   const int nb = (int)c.sp.nbits, pairs = c.vals_in != nullptr ? 1 : 0, sc = size_class(c.n);
   std::lock_guard<std::mutex> lock(g_mu);
   if (c.kind >= 0 && c.kind < kKinds && nb < kNbits && g_set[c.kind][pairs][nb][sc]) return g_table[c.kind][pairs][nb][sc];
-  return default_variant(nb);
+  return default_variant(nb, pairs);
 }
 
 }  // namespace ms
@@ -49,8 +59,8 @@ extern "C" ms_status ms_tune_set(int kind, int pairs, int nbits, int sclass, int
   if (kind < 0 || kind >= kKinds || pairs < 0 || pairs > 1 || nbits < 0 || nbits >= kNbits || sclass < 0 ||
       sclass >= kClasses || shape < 0 || shape > 2 || rank < 0 || rank > 1 || reorder < 0 || reorder > 1)
     return MS_ERR_INVALID_ARG;
-  if (rank == kRankBallot && nbits > 3) return MS_ERR_INVALID_ARG;
-  if (rank == kRankTable && reorder == 0) return MS_ERR_INVALID_ARG;
+  if (rank == kRankBallot && nbits > 5) return MS_ERR_INVALID_ARG;
+  if (reorder == 0 && (rank == kRankTable || nbits > 3)) return MS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
   g_table[kind][pairs][nbits][sclass] = Variant{shape, rank, reorder};
   g_set[kind][pairs][nbits][sclass] = true;
@@ -64,7 +74,7 @@ extern "C" ms_status ms_tune_get(int kind, int pairs, int nbits, int sclass, int
   Variant v;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    v = g_set[kind][pairs][nbits][sclass] ? g_table[kind][pairs][nbits][sclass] : default_variant(nbits);
+    v = g_set[kind][pairs][nbits][sclass] ? g_table[kind][pairs][nbits][sclass] : default_variant(nbits, pairs);
   }
   if (shape) *shape = v.shape;
   if (rank) *rank = v.rank;

@@ -1,0 +1,85 @@
+"""The batched multisplit: every segment of a plan equals the oracle's
+multisplit of that segment alone (bit exact), for keys and pairs, every
+bucket kind, segment sizes from 0 to several tiles, through the direct launch
+and the CUDA-graph replay, twice in a row."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from parity import Case, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [0, 1, 31, 4095, 4096, 4097, 10000, 3 * 4096 + 5, 70000, 255, 2]
+
+
+def cases():
+    return [Case(oracle.MOD, 32), Case(oracle.RANGE_U32, 8, splitters=synthetic.range_splitters(8, 1)),
+            Case(oracle.RADIX, 256, shift=24, bits=8),
+            Case(oracle.DELTA_F32, 64, x0=0.0, delta=float(np.float32(1000.0) / np.float32(64))),
+            Case(oracle.MOD, 1)]
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+@pytest.mark.parametrize("ci", range(5))
+def test_batch_matches_oracle(ci, pairs):
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+
+    case = cases()[ci]
+    keys = [synthetic.uniform_f32_1000(n, 10 + i) if case.kind == oracle.DELTA_F32 else synthetic.uniform_u32(n, 10 + i)
+            for i, n in enumerate(SIZES)]
+    vals = [synthetic.index_values(n) for n in SIZES] if pairs else None
+    dk = [to_dev(k) for k in keys]
+    dv = [to_dev(v) for v in vals] if pairs else None
+    plan = ms.BatchPlan(dk, dv, case.gpu_spec())
+    try:
+        for graph in (False, True, True):
+            for t in plan.keys_out:
+                t.fill_(-1)
+            plan.run(graph=graph)
+            torch.cuda.synchronize()
+            assert ms.device_status() == ms.MS_OK
+            for i, n in enumerate(SIZES):
+                ok, ov, ooff = oracle.multisplit(keys[i], None if vals is None else vals[i], case.oracle_spec())
+                np.testing.assert_array_equal(to_host(plan.keys_out[i]), ok, err_msg=f"segment {i} n={n}")
+                if pairs:
+                    np.testing.assert_array_equal(to_host(plan.vals_out[i]), ov, err_msg=f"segment {i} values")
+                np.testing.assert_array_equal(to_host(plan.offsets[i]).astype(np.uint64), ooff)
+    finally:
+        plan.close()
+
+
+def test_batch_config_4096_segments_small():
+    """The batched configuration's shape at a tenth of its total size: 4096
+    segments with log-uniform sizes in [2^8, 2^16], key mod 32, pairs."""
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+
+    sizes = synthetic.segment_sizes(4096, 8, 16, 42)
+    keys = [synthetic.uniform_u32(int(n), 1000 + i) for i, n in enumerate(sizes)]
+    vals = [synthetic.index_values(int(n)) for n in sizes]
+    plan = ms.BatchPlan([to_dev(k) for k in keys], [to_dev(v) for v in vals], ms.BucketSpec.mod(32))
+    try:
+        plan.run(graph=True)
+        torch.cuda.synchronize()
+        assert ms.device_status() == ms.MS_OK
+        for i in range(0, 4096, 97):
+            ok, ov, ooff = oracle.multisplit(keys[i], vals[i], oracle.Spec(oracle.MOD, 32))
+            np.testing.assert_array_equal(to_host(plan.keys_out[i]), ok)
+            np.testing.assert_array_equal(to_host(plan.vals_out[i]), ov)
+            np.testing.assert_array_equal(to_host(plan.offsets[i]).astype(np.uint64), ooff)
+    finally:
+        plan.close()
+
+
+def test_batch_rejects_mixed_segments():
+    import paper_1701_01189_gb300 as ms
+
+    spec = ms.BucketSpec.mod(4).c()
+    st, _ = ms.ms_batch_plan_create([(0x1000, 0x2000, 0x3000, 0x4000, None, 4), (0x5000, None, 0x6000, None, None, 4)],
+                                    spec)
+    assert st == ms.MS_ERR_INVALID_ARG

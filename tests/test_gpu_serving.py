@@ -1,0 +1,62 @@
+"""Serving: requests that arrive while others are on the GPU are batched into
+the persistent kernel on several streams, and every result equals the plain
+entry point's result on that request alone (bit exact)."""
+import numpy as np
+import pytest
+
+import synthetic
+from parity import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def test_served_results_equal_alone():
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+    from paper_1701_01189_gb300 import serving
+
+    pool = 1 << 20
+    pk = to_dev(synthetic.uniform_u32(pool, 1))
+    pv = to_dev(synthetic.uniform_u32(pool, 2))
+    spl = {m: to_dev(synthetic.range_splitters(m, m)) for m in (8, 32, 256)}
+    trace = serving.make_trace(3000, 0.15, 5, pool=pool, n_lo=6, n_hi=18)
+    arena_bytes = 256 << 20
+    words = sum(2 * r.n + (2 * r.n if r.kind == "sort" else 0) for r in trace)
+    assert words < arena_bytes // 4  # no request's output is overwritten by a later one
+    svc = serving.Service(pk, pv, spl, arena_bytes=arena_bytes, slots=3, max_batch_segments=64,
+                          max_batch_elements=1 << 21)
+    summary = svc.serve(trace, real_time=True)
+    assert summary["requests"] == len(trace)
+    assert ms.device_status() == ms.MS_OK
+    specs = {m: ms.BucketSpec.range_u32(t) for m, t in spl.items()}
+    checked = 0
+    for r in trace:
+        ko, vo = svc.out_views(r)
+        got_k, got_v = to_host(ko), to_host(vo)
+        kin = pk[r.in_off:r.in_off + r.n]
+        vin = pv[r.in_off:r.in_off + r.n]
+        if r.kind == "multisplit":
+            ek, ev, _ = ms.multisplit_pairs(kin, vin, specs[r.m])
+        else:
+            ek, ev = ms.radix_sort(kin, vin, 0, 32)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got_k, to_host(ek), err_msg=f"request {r.rid} {r.kind} m={r.m} n={r.n}")
+        np.testing.assert_array_equal(got_v, to_host(ev))
+        checked += 1
+    assert checked == len(trace)
+    svc.close()
+
+
+def test_serial_baseline_runs():
+    import paper_1701_01189_gb300 as ms
+    from paper_1701_01189_gb300 import serving
+
+    pool = 1 << 18
+    pk = to_dev(synthetic.uniform_u32(pool, 3))
+    pv = to_dev(synthetic.uniform_u32(pool, 4))
+    spl = {m: to_dev(synthetic.range_splitters(m, m)) for m in (8, 32, 256)}
+    trace = serving.make_trace(2000, 0.05, 6, pool=pool, n_lo=6, n_hi=16)
+    summary = serving.serve_serial(trace, pk, pv, spl, real_time=True)
+    assert summary["requests"] == len(trace) and summary["p99_ms"] >= summary["p50_ms"]
+    assert ms.device_status() == ms.MS_OK

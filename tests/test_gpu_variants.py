@@ -13,16 +13,13 @@ pytestmark = pytest.mark.gpu
 
 
 def variants(log2m):
-    out = []
-    for shape in (0, 1, 2):
-        out.append((shape, 1, 1))
-        if log2m <= 3:
-            out += [(shape, 0, 1), (shape, 0, 0)]
-    return out
+    from paper_1701_01189_gb300.autotune import variants as tuner_variants
+
+    return tuner_variants(log2m)
 
 
 CASES = []
-for m, kind in itertools.product([1, 2, 3, 8, 33, 256], ["range", "mod", "radix", "delta"]):
+for m, kind in itertools.product([1, 2, 3, 8, 17, 32, 33, 256], ["range", "mod", "radix", "delta"]):
     if kind == "radix" and m & (m - 1):
         continue
     CASES.append((kind, m))
