@@ -143,9 +143,10 @@ typedef struct ms_batch_plan ms_batch_plan;
  * builds the work list: one item per 4096-key tile for the tile histograms of
  * segments longer than one tile, one per tile for the post-scans.  Allocates
  * the plan's device memory with cudaMalloc and uploads the list
- * (synchronous; do it once, outside any capture).  Errors:
- * MS_ERR_INVALID_ARG (bad spec, NULL/overlapping buffers, mixed keys-only and
- * key-value segments), MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
+ * (synchronous; do it once, outside any capture).  The plan is key-value if
+ * any segment has vals_in; every non-empty segment must then carry values.
+ * Errors: MS_ERR_INVALID_ARG (bad spec, NULL/overlapping buffers, mixed
+ * keys-only and key-value segments), MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
 ms_status ms_batch_plan_create(const ms_segment *segs, uint32_t num_segments, const ms_bucket_spec *spec,
                                ms_batch_plan **plan);
 

@@ -337,7 +337,8 @@ static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec&
   for (uint32_t i = 0; i < num; ++i) {
     const ms_segment& g = segs[i];
     if (g.n >= ((size_t)1 << 32)) return MS_ERR_INVALID_ARG;
-    if ((g.vals_in != nullptr) != pairs || (g.vals_out != nullptr) != pairs) return MS_ERR_INVALID_ARG;
+    // an empty segment may leave every pointer NULL
+    if (g.n > 0 && ((g.vals_in != nullptr) != pairs || (g.vals_out != nullptr) != pairs)) return MS_ERR_INVALID_ARG;
     const size_t bytes = g.n * 4;
     if (g.n > 0 && (g.keys_in == nullptr || g.keys_out == nullptr || overlap(g.keys_in, g.keys_out, bytes)))
       return MS_ERR_INVALID_ARG;
@@ -407,7 +408,8 @@ extern "C" ms_status ms_batch_plan_create(const ms_segment* segs, uint32_t num_s
   int kind = 0;
   ms_status st = make_devspec(spec, &sp, &kind);
   if (st != MS_OK) return st;
-  const bool pairs = num_segments > 0 && segs[0].vals_in != nullptr;
+  bool pairs = false;  // key-value if any segment carries values
+  for (uint32_t i = 0; i < num_segments; ++i) pairs = pairs || segs[i].vals_in != nullptr;
   std::vector<DevSeg> hs(num_segments);
   std::vector<uint2> items;
   uint64_t hwords = 0;

@@ -302,7 +302,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   static_assert(NW == 8 || NW == 16 || NW == 32, "NW must be 8, 16 or 32");
   static_assert(RANK == kRankTable || NB <= 5, "ballot ranks need m <= 32");
   static_assert(STAGES >= 1 && STAGES <= 4, "1..4 ring slots");
-  constexpr int LOGNW = NW == 8 ? 3 : NW == 16 ? 4 : 5;
   extern __shared__ __align__(16) uint32_t smem[];
   const DevSpec& sp = a.sp;
   const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1, lb = sp.lut_bits;

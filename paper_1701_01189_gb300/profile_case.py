@@ -1,0 +1,93 @@
+"""Runs one multisplit or radix-sort case repeatedly, for profiling (e.g. under
+Nsight Compute) and quick timing.
+
+    python -m paper_1701_01189_gb300.profile_case --kind range --m 32 --n-log2 26 --reps 3
+    python -m paper_1701_01189_gb300.profile_case --kind sort --pairs --n-log2 24
+
+Prints the mean time per call (CUDA events) and the per-stage times of the
+library's stage timer.  Inputs are the seeded uniform keys of ``synthetic``.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--kind", choices=["range", "radix", "mod", "delta", "sort"], default="range")
+    ap.add_argument("--m", type=int, default=32)
+    ap.add_argument("--pairs", action="store_true")
+    ap.add_argument("--n-log2", type=int, default=26)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    args = ap.parse_args(argv)
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import numpy as np
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+    import synthetic
+    from paper_1701_01189_gb300 import autotune
+    from paper_1701_01189_gb300.build import build
+
+    build()
+    autotune.load()
+    n = 1 << args.n_log2
+    gen = synthetic.uniform_f32_1000 if args.kind == "delta" else synthetic.uniform_u32
+    dk = torch.from_numpy(gen(n, 1).view(np.int32)).cuda()
+    dv = torch.arange(n, dtype=torch.int32, device="cuda") if args.pairs else None
+    ko = torch.empty_like(dk)
+    vo = torch.empty_like(dk) if args.pairs else None
+    off = torch.empty(257, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    if args.kind == "range":
+        spec = ms.BucketSpec.range_u32(torch.from_numpy(synthetic.range_splitters(args.m, 3).view(np.int32)).cuda())
+    elif args.kind == "radix":
+        spec = ms.BucketSpec.radix(0, int(np.log2(args.m)))
+    elif args.kind == "mod":
+        spec = ms.BucketSpec.mod(args.m)
+    else:
+        spec = ms.BucketSpec.delta_f32(args.m, float(np.float32(1000.0) / np.float32(args.m)))
+    cs = spec.c()
+
+    def run():
+        if args.kind == "sort":
+            st = ms.ms_radix_sort(dk.data_ptr(), dv.data_ptr() if args.pairs else None, n, 0, 32, ko.data_ptr(),
+                                  vo.data_ptr() if args.pairs else None, stream)
+        elif args.pairs:
+            st = ms.ms_multisplit_pairs(dk.data_ptr(), dv.data_ptr(), n, cs, ko.data_ptr(), vo.data_ptr(),
+                                        off.data_ptr(), stream)
+        else:
+            st = ms.ms_multisplit_keys(dk.data_ptr(), n, cs, ko.data_ptr(), off.data_ptr(), stream)
+        if st != ms.MS_OK:
+            raise ms.MsError(st, "profile_case")
+
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    ms.ms_stage_timing(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms.ms_stage_timing(0)
+    t = e0.elapsed_time(e1) / args.reps
+    pre, scan, post, cnt = ms.ms_stage_times()
+    desc = f"{args.kind} m={args.m if args.kind != 'sort' else 256} {'pairs' if args.pairs else 'keys'} n=2^{args.n_log2}"
+    line = f"{desc}: {t:.4f} ms per call = {n / t / 1e6:.1f} G elements/s"
+    if cnt:
+        line += f"; per multisplit: pre-scan {pre / cnt:.4f} ms, scan {scan / cnt:.4f} ms, post-scan {post / cnt:.4f} ms"
+    print(line)
+    if ms.device_status() != ms.MS_OK:
+        raise SystemExit("device status not OK")
+
+
+if __name__ == "__main__":
+    main()

@@ -212,9 +212,11 @@ class Service:
         ev.record(slot.stream)
         slot.event = ev
 
-    def serve(self, trace, real_time: bool = True):
+    def serve(self, trace, real_time: bool = True, on_complete=None):
         """Serves the trace; returns a summary dict.  With real_time, arrivals are
-        released at their trace time; otherwise all at once."""
+        released at their trace time; otherwise all at once.  on_complete(request)
+        is called for every request once its results are in the arena, before its
+        memory is released (out_views(request) gives them)."""
         reqs = sorted(trace, key=lambda r: r.arrival)
         queue = deque()
         i = 0
@@ -234,6 +236,8 @@ class Service:
                     tdone = time.perf_counter() - t0
                     for r in s.reqs:
                         r.done = tdone
+                        if on_complete is not None:
+                            on_complete(r)
                     for rec in s.recs:
                         self.ring.free(rec)
                     remaining -= len(s.reqs)

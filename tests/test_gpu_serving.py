@@ -21,19 +21,21 @@ def test_served_results_equal_alone():
     pv = to_dev(synthetic.uniform_u32(pool, 2))
     spl = {m: to_dev(synthetic.range_splitters(m, m)) for m in (8, 32, 256)}
     trace = serving.make_trace(3000, 0.15, 5, pool=pool, n_lo=6, n_hi=18)
-    arena_bytes = 256 << 20
-    words = sum(2 * r.n + (2 * r.n if r.kind == "sort" else 0) for r in trace)
-    assert words < arena_bytes // 4  # no request's output is overwritten by a later one
-    svc = serving.Service(pk, pv, spl, arena_bytes=arena_bytes, slots=3, max_batch_segments=64,
+    svc = serving.Service(pk, pv, spl, arena_bytes=64 << 20, slots=3, max_batch_segments=64,
                           max_batch_elements=1 << 21)
-    summary = svc.serve(trace, real_time=True)
-    assert summary["requests"] == len(trace)
+    got = {}
+
+    def keep(r):  # called when r's results are ready, before its memory is reused
+        ko, vo = svc.out_views(r)
+        got[r.rid] = (to_host(ko), to_host(vo))
+
+    summary = svc.serve(trace, real_time=True, on_complete=keep)
+    assert summary["requests"] == len(trace) == len(got)
     assert ms.device_status() == ms.MS_OK
     specs = {m: ms.BucketSpec.range_u32(t) for m, t in spl.items()}
     checked = 0
     for r in trace:
-        ko, vo = svc.out_views(r)
-        got_k, got_v = to_host(ko), to_host(vo)
+        got_k, got_v = got[r.rid]
         kin = pk[r.in_off:r.in_off + r.n]
         vin = pv[r.in_off:r.in_off + r.n]
         if r.kind == "multisplit":
