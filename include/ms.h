@@ -214,9 +214,11 @@ ms_status ms_test_expire_lookback(void *stream);
  * n from ms_tune_size_class: 0 below 2^16, 1 below 2^20, 2 below 2^24, 3
  * otherwise).  A variant is: shape of the post-scan tile (0: 8 warps x 16
  * keys per lane, 1: 16 x 8, 2: 8 x 8), rank mode (0: warp ballots, allowed
- * for ceil(log2 m) <= 5; 1: per-warp peer tables) and reorder (1: reorder each
- * tile in shared memory before writing, 0: write from registers; 0 requires
- * rank mode 0 and ceil(log2 m) <= 3).  Unset entries use built-in defaults.  The tuner in
+ * for ceil(log2 m) <= 5; 1: per-warp peer tables; 2: per-thread bucket
+ * counters with a 256-thread x 16-key tile, allowed for ceil(log2 m) <= 5,
+ * shape ignored) and reorder (1: reorder each tile in shared memory before
+ * writing, 0: write from registers; 0 requires rank mode 0 and
+ * ceil(log2 m) <= 3).  Unset entries use built-in defaults.  The tuner in
  * paper_1701_01189_gb300/autotune.py measures the candidates and sets the
  * fastest.  MS_ERR_INVALID_ARG for out-of-range arguments. */
 int ms_tune_size_class(size_t n);

@@ -2,8 +2,9 @@
 
 For a set of workloads (bucket kind, m, keys or pairs, n) it times every
 variant the library offers -- post-scan tile shape (8 warps x 16 keys, 16 x 8,
-8 x 8), rank mode (warp ballots for m <= 8, per-warp peer tables) and
-reordering (block reorder, or direct writes for ballot ranks) -- with CUDA
+8 x 8), rank mode (warp ballots for m <= 32, per-warp peer tables, or
+per-thread bucket counters for m <= 32) and reordering (block reorder, or
+direct writes for ballot ranks) -- with CUDA
 events on the current stream, and installs the fastest for that workload's key
 (kind, pairs, ceil(log2 m), size class of n) with ``ms_tune_set``.  Results can
 be saved to and loaded from JSON (``tuning.json`` beside this file by default).
@@ -22,7 +23,7 @@ DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.
 
 
 def variants(log2m: int):
-    out = []
+    out = [(0, 2, 1)] if log2m <= 5 else []
     for shape in (0, 1, 2):
         out.append((shape, 1, 1))
         if log2m <= 5:

@@ -103,64 +103,64 @@ struct OnesweepArgs {
   uint32_t aligned;        // inputs 16-byte aligned: full tiles arrive by TMA
 };
 
-// Shared memory (words): mbarrier (16), slot keys T, slot values T (pairs),
-// s_goff 256, s_delta 256, s_warp 32, s_cnt NW*257, s_peer 2*NW*256, reorder
-// keys T, values T (pairs), bucket bytes T.
+// Shared memory (words): a ring of two slots (keys T, then values T for
+// pairs), s_goff 256, s_delta 256, s_warp 32, s_cnt NW*257, s_peer
+// 2*NW*256, bucket bytes T.  The tile is permuted in place in its slot.
 template <bool PAIRS>
 struct OsLayout {
   static constexpr uint32_t T = kOsTile;
-  static constexpr uint32_t kSlot = 16;
-  static constexpr uint32_t kGoff = kSlot + T * (PAIRS ? 2 : 1);
+  static constexpr uint32_t kSlotWords = T * (PAIRS ? 2 : 1);
+  static constexpr uint32_t kGoff = 2 * kSlotWords;
   static constexpr uint32_t kDelta = kGoff + 256;
   static constexpr uint32_t kWarp = kDelta + 256;
   static constexpr uint32_t kCnt = kWarp + 32;
   static constexpr uint32_t kPeer = kCnt + kOsNW * 257;
-  static constexpr uint32_t kReorder = (kPeer + 2 * kOsNW * 256 + 3) & ~3u;
-  static constexpr size_t kBytes = 4u * (size_t)(kReorder + T * (PAIRS ? 2 : 1)) + T;
+  static constexpr uint32_t kBkt = (kPeer + 2 * kOsNW * 256 + 3) & ~3u;
+  static constexpr size_t kBytes = 4u * (size_t)kBkt + T;
 };
 
+// One digit pass, persistent: every CTA takes tiles by ticket (so every
+// earlier tile belongs to a CTA that already started, and the look-back below
+// always ends), and while it works on one tile the copy of its next tile is in
+// flight into the other slot.
 template <bool PAIRS>
 __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(OnesweepArgs a) {
   using Lay = OsLayout<PAIRS>;
   constexpr uint32_t T = Lay::T;
   constexpr int THREADS = kOsNW * 32;
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_tile_id;
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* slot_k = smem + Lay::kSlot;
-  uint32_t* slot_v = slot_k + T;
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tile[2], s_pend[2];
   uint32_t* s_goff = smem + Lay::kGoff;
   uint32_t* s_delta = smem + Lay::kDelta;
   uint32_t* s_warp = smem + Lay::kWarp;
   uint32_t* s_cnt = smem + Lay::kCnt;
   uint32_t* s_peer = smem + Lay::kPeer;
-  uint32_t* s_keys = smem + Lay::kReorder;
-  uint32_t* s_vals = s_keys + T;
-  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(s_keys + T * (PAIRS ? 2 : 1));
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(smem + Lay::kBkt);
   const DevSpec& sp = a.sp;
   const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  const uint32_t L = (uint32_t)(((size_t)a.n + T - 1) / T);
 
-  // Tiles are numbered by ticket, so every earlier tile belongs to a CTA that
-  // already started: the look-back below always makes progress.
-  if (threadIdx.x == 0) {
-    const uint32_t tile = atomicAdd(a.ticket, 1u);
-    s_tile_id = tile;
-    mbar_init(s_bar, 1);
-    fence_mbar_init();
+  // thread 0: start the copy of `tile` into `slot` (full tiles of aligned inputs)
+  auto issue = [&](uint32_t tile, uint32_t slot) {
     const size_t tbase = (size_t)tile * T;
-    if (a.aligned && tbase + T <= a.n) {
-      mbar_arrive_expect_tx(s_bar, T * 4u * (PAIRS ? 2u : 1u));
-      bulk_g2s(slot_k, a.keys_in + tbase, T * 4u, s_bar);
-      if constexpr (PAIRS) bulk_g2s(slot_v, a.vals_in + tbase, T * 4u, s_bar);
-    }
-  }
-  __syncthreads();
-  const uint32_t tile = s_tile_id;
-  const size_t tbase = (size_t)tile * T;
-  const uint32_t tile_n = (uint32_t)min((size_t)T, (size_t)a.n - tbase);
-  const bool tma = a.aligned && tile_n == T;
+    if (tile >= L || !a.aligned || tbase + T > a.n) return;
+    uint32_t* sk = smem + slot * Lay::kSlotWords;
+    mbar_arrive_expect_tx(s_bar + slot, T * 4u * (PAIRS ? 2u : 1u));
+    bulk_g2s(sk, a.keys_in + tbase, T * 4u, s_bar + slot);
+    if constexpr (PAIRS) bulk_g2s(sk + T, a.vals_in + tbase, T * 4u, s_bar + slot);
+    s_pend[slot] = 1u;
+  };
 
+  if (threadIdx.x == 0) {
+    mbar_init(s_bar, 1);
+    mbar_init(s_bar + 1, 1);
+    s_pend[0] = s_pend[1] = 0u;
+    fence_mbar_init();
+    s_tile[0] = atomicAdd(a.ticket, 1u);
+    issue(s_tile[0], 0);
+  }
   // digit offsets of this pass (first term of Eq. 2): exclusive scan of the histogram
   {
     const uint32_t v = threadIdx.x < m ? a.hist[threadIdx.x] : 0u;
@@ -169,97 +169,138 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
     if (threadIdx.x < m) s_goff[threadIdx.x] = ex;
   }
   for (uint32_t i = threadIdx.x; i < 2 * kOsNW * m_pad; i += THREADS) s_peer[i] = 0u;
-  if (a.status_next != nullptr)
-    for (uint32_t d = threadIdx.x; d < 256; d += THREADS) a.status_next[(size_t)tile * 256 + d] = 0u;
-  bool ok = true;
-  if (tma) {
-    ok = mbar_wait(s_bar, 0, a.err);
-  } else {
-    for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
-      slot_k[p] = __ldcs(a.keys_in + tbase + p);
-      if constexpr (PAIRS) slot_v[p] = __ldcs(a.vals_in + tbase + p);
-    }
-  }
   __syncthreads();
 
   uint32_t* wc = s_cnt + w * S;
   uint32_t* wpeer = s_peer + w * 2 * m_pad;
   const uint32_t off0 = w * (32 * kOsItems) + lane;
-  const uint32_t avail = tile_n - min(tile_n, w * (32u * kOsItems));
-  uint32_t rb[kOsItems];
   const uint32_t lane_x[1] = {0u};
-  if (tile_n == T)
-    rank_windows<kRadix, 8, kOsItems, kRankTable, true>(slot_k + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad,
-                                                       m, lane_x, lanemask_lt(), lane, rb);
-  else
-    rank_windows<kRadix, 8, kOsItems, kRankTable, false>(slot_k + off0, avail, sp, nullptr, nullptr, wc, wpeer,
-                                                        m_pad, m, lane_x, lanemask_lt(), lane, rb);
-  if (__syncthreads_or(!ok)) return;  // a copy never arrived (the error bit is set)
-  const uint32_t total = scan_tile_counters<kOsNW>(s_cnt, S, m_pad, s_warp);
+  uint32_t phase = 0;  // bit k: parity of slot k's next completion
 
-  // Decoupled look-back per digit: publish this tile's count, add up the
-  // earlier tiles' counts until one carries an inclusive prefix.
-  if (threadIdx.x < m) {
-    const uint32_t d = threadIdx.x;
-    const uint32_t tstart = s_cnt[d];
-    const uint32_t hist = ((d + 1 < m_pad) ? s_cnt[d + 1] : total) - tstart;
-    uint32_t* st = a.status + (size_t)tile * 256 + d;
-    uint32_t excl = 0;
-    if (tile == 0) {
-      st_relaxed_u32(st, kOsPrefix | hist);
+  for (uint32_t k = 0;; ++k) {
+    const uint32_t slot = k & 1u;
+    const uint32_t tile = s_tile[slot];
+    if (tile >= L) break;
+    if (threadIdx.x == 0) {
+      // the other slot was emptied before the last barrier: prefetch the next tile
+      const uint32_t nx = atomicAdd(a.ticket, 1u);
+      s_tile[slot ^ 1u] = nx;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(nx, slot ^ 1u);
+    }
+    uint32_t* sk = smem + slot * Lay::kSlotWords;
+    uint32_t* sv = sk + T;
+    (void)sv;
+    const size_t tbase = (size_t)tile * T;
+    const uint32_t tile_n = (uint32_t)min((size_t)T, (size_t)a.n - tbase);
+    const bool tma = a.aligned && tile_n == T;
+    if (a.status_next != nullptr)
+      for (uint32_t d = threadIdx.x; d < 256; d += THREADS) a.status_next[(size_t)tile * 256 + d] = 0u;
+    bool ok = true;
+    if (tma) {
+      ok = mbar_wait(s_bar + slot, (phase >> slot) & 1u, a.err);
+      if (ok) phase ^= 1u << slot;
     } else {
-      st_relaxed_u32(st, kOsAggregate | hist);
-      for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
-        const uint32_t* q = a.status + (size_t)p * 256 + d;
-        uint32_t v = ld_relaxed_u32(q);
-        uint32_t spins = 0;
-        while ((v & ~kOsValue) == 0u) {
-          // give up at the bound, or at once when another wait has already given up
-          if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
-            atomicOr(a.err, kDevErrTimeout);
-            v = kOsPrefix;
-            break;
-          }
-          __nanosleep(spins < 64 ? 32 : 256);
-          v = ld_relaxed_u32(q);
-        }
-        excl += v & kOsValue;
-        if ((v & ~kOsValue) == kOsPrefix) break;
+      for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
+        sk[p] = __ldcs(a.keys_in + tbase + p);
+        if constexpr (PAIRS) sv[p] = __ldcs(a.vals_in + tbase + p);
       }
-      st_relaxed_u32(st, kOsPrefix | ((excl + hist) & kOsValue));
+      __syncthreads();
     }
-    s_delta[d] = s_goff[d] + excl - tstart;
-  }
-  __syncthreads();
 
-  // reorder the tile by digit in shared memory, then coalesced writes
-#pragma unroll
-  for (int i = 0; i < kOsItems; ++i) {
-    if (off0 + i * 32 < tile_n) {
-      const uint32_t b = rb[i] >> 16;
-      const uint32_t p = wc[b] + (rb[i] & 0xffffu);
-      if (p < T) {
-        s_keys[p] = slot_k[off0 + i * 32];
-        if constexpr (PAIRS) s_vals[p] = slot_v[off0 + i * 32];
-        s_bkt[p] = (uint8_t)b;
+    const uint32_t avail = tile_n - min(tile_n, w * (32u * kOsItems));
+    uint32_t rb[kOsItems];
+    if (tile_n == T)
+      rank_windows<kRadix, 8, kOsItems, kRankTable, true>(sk + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad, m,
+                                                         lane_x, lanemask_lt(), lane, rb);
+    else
+      rank_windows<kRadix, 8, kOsItems, kRankTable, false>(sk + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad,
+                                                          m, lane_x, lanemask_lt(), lane, rb);
+    if (__syncthreads_or(!ok)) {
+      // a copy never arrived (the error bit is set): drain the copies in flight, stop
+      if (threadIdx.x == 0)
+        for (uint32_t q = 0; q < 2; ++q)
+          if (s_pend[q] != 0u && !(q == slot && ok)) mbar_drain(s_bar + q, (phase >> q) & 1u);
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0) s_pend[slot] = 0u;
+    const uint32_t total = scan_tile_counters<kOsNW>(s_cnt, S, m_pad, s_warp);
+
+    // Decoupled look-back per digit: publish this tile's count, add up the
+    // earlier tiles' counts until one carries an inclusive prefix.
+    if (threadIdx.x < m) {
+      const uint32_t d = threadIdx.x;
+      const uint32_t tstart = s_cnt[d];
+      const uint32_t hist = ((d + 1 < m_pad) ? s_cnt[d + 1] : total) - tstart;
+      uint32_t* st = a.status + (size_t)tile * 256 + d;
+      uint32_t excl = 0;
+      if (tile == 0) {
+        st_relaxed_u32(st, kOsPrefix | hist);
       } else {
-        atomicOr(a.err, kDevErrBounds);
+        st_relaxed_u32(st, kOsAggregate | hist);
+        for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
+          const uint32_t* q = a.status + (size_t)p * 256 + d;
+          uint32_t v = ld_relaxed_u32(q);
+          uint32_t spins = 0;
+          while ((v & ~kOsValue) == 0u) {
+            // give up at the bound, or at once when another wait has already given up
+            if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
+              atomicOr(a.err, kDevErrTimeout);
+              v = kOsPrefix;
+              break;
+            }
+            __nanosleep(spins < 64 ? 32 : 256);
+            v = ld_relaxed_u32(q);
+          }
+          excl += v & kOsValue;
+          if ((v & ~kOsValue) == kOsPrefix) break;
+        }
+        st_relaxed_u32(st, kOsPrefix | ((excl + hist) & kOsValue));
+      }
+      s_delta[d] = s_goff[d] + excl - tstart;
+    }
+    // this thread's keys (and values) into registers before the in-place permutation
+    uint32_t kr[kOsItems];
+    uint32_t vr[PAIRS ? kOsItems : 1];
+#pragma unroll
+    for (int i = 0; i < kOsItems; ++i) {
+      if (off0 + i * 32 < tile_n) {
+        kr[i] = sk[off0 + i * 32];
+        if constexpr (PAIRS) vr[i] = sv[off0 + i * 32];
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
+    // reorder the tile by digit in place, then coalesced writes
 #pragma unroll
-  for (int k = 0; k < kOsItems; ++k) {
-    const uint32_t p = threadIdx.x + k * THREADS;
-    if (p < tile_n) {
-      const uint32_t g = s_delta[s_bkt[p]] + p;
-      if (g < a.n) {
-        __stcs(a.keys_out + g, s_keys[p]);
-        if constexpr (PAIRS) __stcs(a.vals_out + g, s_vals[p]);
-      } else {
-        atomicOr(a.err, kDevErrBounds);
+    for (int i = 0; i < kOsItems; ++i) {
+      if (off0 + i * 32 < tile_n) {
+        const uint32_t b = rb[i] >> 16;
+        const uint32_t p = wc[b] + (rb[i] & 0xffffu);
+        if (p < T) {
+          sk[p] = kr[i];
+          if constexpr (PAIRS) sv[p] = vr[i];
+          s_bkt[p] = (uint8_t)b;
+        } else {
+          atomicOr(a.err, kDevErrBounds);
+        }
       }
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kOsItems; ++q) {
+      const uint32_t p = threadIdx.x + q * THREADS;
+      if (p < tile_n) {
+        const uint32_t g = s_delta[s_bkt[p]] + p;
+        if (g < a.n) {
+          __stcs(a.keys_out + g, sk[p]);
+          if constexpr (PAIRS) __stcs(a.vals_out + g, sv[p]);
+        } else {
+          atomicOr(a.err, kDevErrBounds);
+        }
+      }
+    }
+    __syncthreads();  // the slot, s_bkt and s_delta are free again
   }
 }
 
@@ -287,10 +328,12 @@ cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, 
   uint32_t* tmp_v = pairs ? tmp_k + n : nullptr;
   e = cudaMemsetAsync(ws, 0, hist_b + 2 * status_b + tick_b, s);
 
+  int occ_keys = 1, occ_pairs = 1;  // CTAs of the pass kernel resident per SM
   {
-    // dynamic shared memory opt-in, once per device
+    // dynamic shared memory opt-in and occupancy, once per device
     static std::mutex mu;
     static uint64_t ready = 0;
+    static int g_occ[64][2];
     std::lock_guard<std::mutex> lock(mu);
     const int d = ctx.device & 63;
     if (!((ready >> d) & 1ull)) {
@@ -299,8 +342,17 @@ cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, 
                            (int)OsLayout<false>::kBytes);
       cudaFuncSetAttribute(k_onesweep_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)OsLayout<true>::kBytes);
+      int v = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_onesweep_pass<false>, kOsNW * 32,
+                                                        OsLayout<false>::kBytes) == cudaSuccess && v > 0)
+        g_occ[d][0] = v;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_onesweep_pass<true>, kOsNW * 32,
+                                                        OsLayout<true>::kBytes) == cudaSuccess && v > 0)
+        g_occ[d][1] = v;
       ready |= 1ull << d;
     }
+    occ_keys = g_occ[d][0];
+    occ_pairs = g_occ[d][1];
   }
   if (e == cudaSuccess) {
     RadixHistArgs ha{keys_in, n, (uint32_t)begin_bit, (uint32_t)end_bit, passes, hist};
@@ -338,10 +390,11 @@ cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, 
     oa.ticket = tickets + p;
     oa.err = ctx.d_err;
     oa.aligned = aligned;
+    const uint32_t grid = std::max(1u, std::min(L, (uint32_t)ctx.sm_count * (uint32_t)(pairs ? occ_pairs : occ_keys)));
     if (pairs)
-      k_onesweep_pass<true><<<L, kOsNW * 32, OsLayout<true>::kBytes, s>>>(oa);
+      k_onesweep_pass<true><<<grid, kOsNW * 32, OsLayout<true>::kBytes, s>>>(oa);
     else
-      k_onesweep_pass<false><<<L, kOsNW * 32, OsLayout<false>::kBytes, s>>>(oa);
+      k_onesweep_pass<false><<<grid, kOsNW * 32, OsLayout<false>::kBytes, s>>>(oa);
     e = cudaGetLastError();
     src_k = dst_k;
     src_v = dst_v;

@@ -52,6 +52,12 @@ static inline Chunking make_chunking(uint32_t n, uint32_t T, uint32_t max_ctas) 
   return ch;
 }
 
+}  // namespace ms
+
+#include "ms_run_tc.cuh"
+
+namespace ms {
+
 // Pre-scan tile: 8 warps x 16 keys per lane.  Its NB only sizes the splitter
 // search of range buckets; 8 covers every m.
 constexpr int kPreNW = 8, kPreItems = 16, kPreMinB = 3;
@@ -153,6 +159,7 @@ static cudaError_t run_ms_ballot(const Call& c, DeviceCtx& ctx, const Variant& v
 template <int KIND>
 static cudaError_t run_ms_kind(const Call& c, DeviceCtx& ctx) {
   const Variant v = choose_variant(c);
+  if (v.rank == kRankThread && c.sp.m <= kTcMaxM) return run_tc<KIND>(c, ctx);
   if (v.rank == kRankBallot && c.sp.nbits <= 5) {
     switch (c.sp.nbits) {
       case 0: return run_ms_ballot<KIND, 0>(c, ctx, v);

@@ -1,0 +1,138 @@
+// ms_run_tc.cuh -- host launcher of the per-thread-counter multisplit kernels
+// (ms_tc.cuh) for m <= 32: one small memset, the pre-scan (whose last CTA
+// scans H), and the post-scan launched as a programmatic dependent of the
+// pre-scan.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "ms_host.h"
+#include "ms_tc.cuh"
+
+namespace ms {
+
+// cuTensorMapEncodeTiled from the driver, looked up once (nullptr if missing:
+// the kernels then copy tiles with plain loads).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of a uint32 array seen as rows of 32 words (floor(n / 32) rows),
+// box 32 x 128 (one 4096-key tile), 128-byte swizzle.  False if it cannot be
+// made (then the caller copies tiles with plain loads).
+inline bool make_tile_map(CUtensorMap* map, const uint32_t* base, uint32_t n) {
+  auto enc = tensor_map_encoder();
+  if (enc == nullptr || n < kTcTile || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  const cuuint64_t dims[2] = {32, n / 32u};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {32, kTcTile / 32u};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(base), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Bytes of L2 the pre-scan asks to keep (evict_last) for the post-scan: the
+// last tiles of every chunk, about half of the 126 MB L2.
+constexpr size_t kTcL2KeepBytes = (size_t)64 << 20;
+
+template <int KIND, bool PAIRS, int STAGES>
+static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
+  constexpr uint32_t T = kTcTile;
+  const bool small_m = c.sp.m <= 8;
+  auto kpre = small_m ? k_prescan_tc<KIND, true> : k_prescan_tc<KIND, false>;
+  auto kpost = k_postscan_tc<KIND, PAIRS, STAGES>;
+  using Lay = TcPostLayout<KIND, PAIRS, STAGES>;
+  const DevSpec& sp = c.sp;
+  // splitter lookup tables: 1024 cells x 8 copies for the pre-scan; 512 cells
+  // x 4 copies for the post-scan (x 2 for key-value pairs with more than 16
+  // buckets, which keeps two CTAs of the post-scan per SM)
+  const uint32_t pre_lb = 10, pre_lw = 3;
+  const uint32_t post_lb = 9, post_lw = (PAIRS && sp.m > 16) ? 1u : 2u;
+  const size_t smem_pre = tc_prescan_smem<KIND>(sp.m, pre_lb, pre_lw);
+  const size_t smem_post = Lay::bytes(sp.m, post_lb, post_lw);
+  static LaunchInfo li_pre_s, li_pre_l, li_post;
+  const int nb_post = setup_kernel(li_post, kpost, kTcThreads, Lay::bytes(kTcMaxM, post_lb, 2), smem_post, ctx.device);
+  setup_kernel(small_m ? li_pre_s : li_pre_l, kpre, kTcThreads, tc_prescan_smem<KIND>(kTcMaxM, pre_lb, pre_lw),
+               smem_pre, ctx.device);
+
+  const Chunking ch = make_chunking(c.n, T, (uint32_t)(ctx.sm_count * nb_post));
+  const uint32_t m = sp.m;
+  // scratch: H (m * G words) | arrival counter
+  const size_t h_bytes = ((size_t)m * ch.G * 4 + 15) & ~(size_t)15;
+  const size_t bytes = h_bytes + 16;
+  void* ws = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (c.ws_fixed != nullptr) {
+    if (bytes > c.ws_capacity) return cudaErrorMemoryAllocation;
+    ws = c.ws_fixed;
+  } else {
+    e = scratch_alloc(ctx, &ws, bytes, c.stream);
+    if (e != cudaSuccess) return e;
+  }
+  uint32_t* H = static_cast<uint32_t*>(ws);
+  uint32_t* arrive = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes);
+  e = cudaMemsetAsync(arrive, 0, 16, c.stream);
+
+  const bool vec = ((reinterpret_cast<uintptr_t>(c.keys_in)) & 15u) == 0;
+  CUtensorMap tmk, tmv;
+  std::memset(&tmk, 0, sizeof tmk);
+  std::memset(&tmv, 0, sizeof tmv);
+  bool tma = make_tile_map(&tmk, c.keys_in, c.n);
+  if (tma && PAIRS) tma = make_tile_map(&tmv, c.vals_in, c.n);
+
+  // the last `keep` tiles of every chunk are read with evict_last
+  const size_t keep_tiles = kTcL2KeepBytes / ((size_t)T * 4);
+  const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
+  const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
+  if (e == cudaSuccess) {
+    TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, arrive, c.offsets, pre_lb, pre_lw, sp};
+    kpre<<<ch.G, kTcThreads, smem_pre, c.stream>>>(pa);
+    e = cudaGetLastError();
+    trace_mark(slot, 1, c.stream);
+    trace_mark(slot, 2, c.stream);  // the global scan runs inside the pre-scan
+  }
+  if (e == cudaSuccess) {
+    TcPostArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, ch.K, ch.L, ch.G, H, ctx.d_err,
+                  tma ? 1u : 0u, post_lb, post_lw, sp};
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3(ch.G);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = smem_post;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = slot < 0 ? 1 : 0;  // stage timing records events between the kernels
+    e = cudaLaunchKernelEx(&cfg, kpost, tmk, tmv, qa);
+    trace_mark(slot, 3, c.stream);
+  }
+  const cudaError_t e2 = c.ws_fixed != nullptr ? cudaSuccess : scratch_free(ws, c.stream);
+  return e != cudaSuccess ? e : e2;
+}
+
+template <int KIND>
+static cudaError_t run_tc(const Call& c, DeviceCtx& ctx) {
+  if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2>(c, ctx);
+  return run_tc_cfg<KIND, false, 2>(c, ctx);
+}
+
+}  // namespace ms

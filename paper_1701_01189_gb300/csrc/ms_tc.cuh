@@ -1,0 +1,612 @@
+// ms_tc.cuh -- the pre-scan and post-scan of the multisplit (Section 4.6 /
+// 5.3) for up to 32 buckets, ranked with per-thread bucket counters.
+//
+// Localization (Section 4.4): CTA c owns a chunk of consecutive 4096-key
+// tiles (first level, one column of H per chunk); a tile is solved as a whole
+// (second level) by 256 threads, thread t owning the 16 consecutive keys
+// [16t, 16t+16) of the tile (third level).  The direct solve of Section 4.5
+// is done with a counter per (bucket, thread) in shared memory instead of the
+// warp ballots of Section 5.4: a thread adds 1 to the counter of each of its
+// keys' buckets with a shared-memory atomic that returns the count before
+// the increment -- the key's rank among the earlier keys of its bucket in
+// that thread -- and one exclusive scan over the counters in (bucket, thread)
+// order then gives every (bucket, thread) its first position in the
+// bucket-ordered tile (both terms of the block-level local offset of Section
+// 5.5.4 at once).  Position = scan value + rank; the tile is permuted in
+// place in shared memory (the block-level reordering of Section 5.6.2) and
+// written out with consecutive threads on consecutive positions, so global
+// writes are coalesced per bucket run.
+//
+// Why on GB300: an SM must move about 22 bytes of HBM traffic per cycle, so a
+// 32-key window may cost only ~35 warp instructions in the post-scan.  The
+// ballot ranks cost about 3 ceil(log2 m) + 10 per window before the reorder;
+// the counter ranks cost two instructions per key (address, atomic) plus
+// m/16 per key for the scan, independent of the key distribution.
+//
+// Tiles arrive in shared memory by TMA tensor copies with the 128-byte
+// swizzle (the 16-byte chunk c of 128-byte row r lands at chunk c ^ (r & 7)),
+// so a thread's 64 contiguous bytes are read with four conflict-free 16-byte
+// loads.  The pre-scan reads the keys straight into registers with 16-byte
+// loads, keeping the last part of every chunk in L2 (evict_last) for the
+// post-scan, which walks its chunk last tile first.  The last pre-scan CTA to
+// finish computes the global scan of H (Section 4.3, Eq. 2), so the
+// post-scan, launched as a programmatic dependent, starts its set-up and first
+// copies while the pre-scan drains.
+#pragma once
+
+#include <cuda.h>
+
+#include "ms_bucket.cuh"
+#include "ms_tma.cuh"
+
+namespace ms {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcKpt = 16;                         // keys per thread
+constexpr uint32_t kTcTile = kTcThreads * kTcKpt;  // 4096 keys = 128 rows of 32 words
+constexpr uint32_t kTcRow = 288;                   // words per bucket row: 256 counters + 4 pad words per 32
+constexpr uint32_t kTcMaxM = 32;
+
+// Counter rows (a power of two >= 4 and >= m): the scan covers R * 256 counters.
+__host__ __device__ constexpr uint32_t tc_rows(uint32_t m) { return m <= 4 ? 4u : m <= 8 ? 8u : m <= 16 ? 16u : 32u; }
+
+// Padded index of flattened counter i = b * 256 + t: 4 pad words after every
+// 32 keep both the per-thread atomics (bank = lane) and the 16-byte raking
+// loads (thread r reads R consecutive counters) free of bank conflicts.
+__device__ __forceinline__ uint32_t tc_pad(uint32_t i) { return i + ((i >> 5) << 2); }
+
+// Word position of tile element p in a slot filled by a 128-byte-swizzle tensor
+// copy of 32-word rows (row p >> 5, 16-byte chunk (p >> 2) & 7 XOR row & 7).
+__device__ __forceinline__ uint32_t tc_swz(uint32_t p) { return p ^ (((p >> 5) & 7u) << 2); }
+
+// Word position of element p of the bucket-ordered tile: the low 5 bits XOR
+// the 32-word row index, so the scatter of 32 keys whose positions step by a
+// power of two (few buckets: a thread's keys of one bucket are spread evenly)
+// and the write-out of 32 consecutive positions both hit 32 different banks.
+__device__ __forceinline__ uint32_t tc_rswz(uint32_t p) { return p ^ ((p >> 5) & 31u); }
+
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// 16-byte read-only load that does not allocate in L1, with an L2 policy.
+__device__ __forceinline__ uint4 ldg_v4_policy(const uint32_t* p, uint64_t policy) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(policy));
+  return v;
+}
+
+// One 2-D tensor copy (box 32 words x 128 rows) into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_tile_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+
+// Exclusive scan over the 256 threads with one block barrier.  s_warp (8
+// words) must not be rewritten before the caller's next block barrier.
+__device__ __forceinline__ uint32_t tc_block_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  const uint4 a = *reinterpret_cast<const uint4*>(s_warp);
+  const uint4 b = *reinterpret_cast<const uint4*>(s_warp + 4);
+  const uint32_t ws[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint32_t pre = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    pre += (i < (int)w) ? ws[i] : 0u;
+    tot += ws[i];
+  }
+  *total = tot;
+  return pre + x - v;
+}
+
+// Splitter lookup table of these kernels (range buckets, m <= 32): 2^lb
+// cells of the key space (its top lb bits), each one 32-bit word -- the
+// bucket of the cell's first key (bits 0..4), a flag for a cell holding two
+// or more splitters (bit 5), and the low 32 - lb bits of the cell's single
+// splitter (bits 6..31; 2^(32-lb), above every key, when it holds none) --
+// stored W = 2^lw times side by side: lane l reads copy l mod W, so a warp's
+// random lookups spread over W times as many banks.  A flagged cell's keys
+// take the full search over the splitter table (tc_fixup).  lb >= 7.
+constexpr uint32_t kTcLutFlag = 32u;
+
+__host__ __device__ constexpr uint32_t tc_lut_words(int kind, uint32_t lb, uint32_t lw) {
+  return kind == kRange ? (1u << (lb + lw)) : 0u;
+}
+
+// Splitter table (31 entries, padded with 0xffffffff) and lookup table.  All
+// threads of the block call it; ends with a block barrier.
+template <int KIND>
+__device__ __forceinline__ void tc_build_tables(const DevSpec& sp, uint32_t lb, uint32_t lw, uint32_t* tbl,
+                                                uint32_t* lut) {
+  if constexpr (KIND == kRange) {
+    for (uint32_t i = threadIdx.x; i < 31u; i += blockDim.x) tbl[i] = (i + 1 < sp.m) ? sp.splitters[i] : 0xffffffffu;
+    __syncthreads();
+    const uint32_t sh = 32u - lb, fmask = (1u << sh) - 1u, W = 1u << lw, m = sp.m;
+    for (uint32_t cell = threadIdx.x; cell < (1u << lb); cell += blockDim.x) {
+      const uint32_t first = cell << sh, last = first | fmask;
+      // splitters <= x, clamped to m - 1, is the bucket of x
+      const uint32_t lo = min(first == 0u ? 0u : range_search<5>(first - 1u, tbl, m + 1u), m - 1u);
+      const uint32_t hi = min(range_search<5>(last, tbl, m + 1u), m - 1u);
+      uint32_t e;
+      if (hi == lo)
+        e = lo | ((fmask + 1u) << 6);
+      else if (hi == lo + 1u)
+        e = lo | ((tbl[lo] & fmask) << 6);
+      else
+        e = kTcLutFlag;
+      for (uint32_t r = 0; r < W; ++r) lut[(cell << lw) + r] = e;
+    }
+  }
+  __syncthreads();
+}
+
+// Bucket of u by the fast path.  For range buckets the bucket returned for a
+// key of a flagged cell is wrong; callers OR the table words into `flag` and
+// redo the flagged keys with tc_fixup.
+struct TcLut {
+  const uint32_t* lut;
+  uint32_t sh;    // 32 - lb
+  uint32_t lw;    // log2 of the copies
+  uint32_t rep;   // this lane's copy
+  uint32_t fmask; // 2^sh - 1
+  __device__ __forceinline__ uint32_t word(uint32_t u) const { return lut[((u >> sh) << lw) + rep]; }
+};
+
+template <int KIND>
+__device__ __forceinline__ uint32_t tc_bucket(uint32_t u, const DevSpec& sp, const TcLut& L, uint32_t& flag) {
+  if constexpr (KIND == kRange) {
+    const uint32_t e = L.word(u);
+    flag |= e;
+    return (e & 31u) + ((u & L.fmask) >= (e >> 6) ? 1u : 0u);
+  } else {
+    return bucket_of<KIND, 5>(u, sp, nullptr, nullptr);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void tc_fixup(const uint32_t (&key)[N], uint32_t (&bk)[N], const TcLut& L,
+                                         const uint32_t* tbl, uint32_t m) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (L.word(key[i]) & kTcLutFlag) bk[i] = range_search<5>(key[i], tbl, m);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pre-scan: per-chunk bucket histograms (column c of H, bucket-major
+// H[b * G + c]), then, in the last CTA to finish, the exclusive scan of the
+// row-vectorised H in place and the bucket offsets.
+struct TcPreArgs {
+  const uint32_t* keys;
+  uint32_t n;
+  uint32_t tiles_per_chunk;  // K
+  uint32_t num_tiles;        // L
+  uint32_t G;                // chunks (CTAs)
+  uint32_t keep_from;        // chunk-relative tile index from which loads keep their lines in L2
+  uint32_t vec;              // keys 16-byte aligned
+  uint32_t* H;               // m * G words; becomes the exclusive scan
+  uint32_t* arrive;          // zero before the launch
+  uint32_t* offsets;         // m + 1 words, or nullptr
+  uint32_t lb, lw;           // lookup table: 2^lb cells, 2^lw copies (range buckets)
+  DevSpec sp;
+};
+
+template <int KIND>
+__host__ size_t tc_prescan_smem(uint32_t m, uint32_t lb, uint32_t lw) {
+  return 4u * (size_t)(tc_rows(m) * kTcRow + 32u + tc_lut_words(KIND, lb, lw));
+}
+
+// SMALLM (m <= 8): each thread counts its keys in one 64-bit register of
+// eight 8-bit fields (no shared-memory traffic per key), flushed into its
+// shared counters before a field can overflow.
+template <int KIND, bool SMALLM>
+__global__ void __launch_bounds__(kTcThreads, 3) k_prescan_tc(TcPreArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_last;
+  const DevSpec& sp = a.sp;
+  const uint32_t m = sp.m, R = tc_rows(m);
+  uint32_t* s_cnt = smem;
+  uint32_t* s_tbl = smem + R * kTcRow;
+  uint32_t* s_lut = s_tbl + 32;
+  const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
+  const TcLut L{s_lut, 32u - a.lb, a.lw, lane & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u};
+
+  for (uint32_t i = t; i < R * kTcRow; i += kTcThreads) s_cnt[i] = 0u;
+  tc_build_tables<KIND>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
+  pdl_launch_dependents();
+
+  uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)
+  const uint32_t c = blockIdx.x;
+  const uint32_t t0 = c * a.tiles_per_chunk;
+  const uint32_t t1 = min(t0 + a.tiles_per_chunk, a.num_tiles);
+  const uint32_t nfull = a.n / kTcTile;  // tiles [0, nfull) are full
+  const uint32_t tv1 = a.vec ? max(t0, min(t1, nfull)) : t0;
+  const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
+
+  uint64_t creg = 0;     // SMALLM: eight 8-bit counters
+  uint32_t creg_keys = 0;  // keys in creg since its last flush
+  auto flush = [&]() {
+    for (uint32_t b = 0; b < m; ++b) {
+      const uint32_t v = (uint32_t)(creg >> (8u * b)) & 0xffu;
+      if (v) atomicAdd(my + b * kTcRow, v);
+    }
+    creg = 0;
+    creg_keys = 0;
+  };
+  auto count16 = [&](uint32_t (&key)[16]) {
+    uint32_t bk[16];
+    uint32_t flag = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+    if constexpr (KIND == kRange)
+      if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
+    if constexpr (SMALLM) {
+      if (creg_keys + 16u > 255u) flush();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) creg += 1ull << (8u * bk[i]);
+      creg_keys += 16u;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) atomicAdd(my + bk[i] * kTcRow, 1u);
+    }
+  };
+  // thread (w, lane) holds words w*512 + j*128 + 4*lane + e of the tile
+  auto load16 = [&](uint32_t (&key)[16], uint32_t tile) {
+    const uint64_t pol = (tile - t0 >= a.keep_from) ? pol_last : pol_first;
+    const uint32_t* src = a.keys + (size_t)tile * kTcTile + w * 512u + 4u * lane;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 v = ldg_v4_policy(src + 128 * j, pol);
+      key[4 * j + 0] = v.x;
+      key[4 * j + 1] = v.y;
+      key[4 * j + 2] = v.z;
+      key[4 * j + 3] = v.w;
+    }
+  };
+
+  // full, aligned tiles: 16-byte loads, the next tile's loads in flight while
+  // this one is counted
+  if (t0 < tv1) {
+    uint32_t ka[16], kb[16];
+    load16(ka, t0);
+    for (uint32_t tile = t0; tile < tv1; tile += 2) {
+      if (tile + 1 < tv1) load16(kb, tile + 1);
+      count16(ka);
+      if (tile + 1 >= tv1) break;
+      if (tile + 2 < tv1) load16(ka, tile + 2);
+      count16(kb);
+    }
+  }
+  // the partial last tile, or every tile of an unaligned input
+  for (uint32_t tile = tv1; tile < t1; ++tile) {
+    const size_t tb = (size_t)tile * kTcTile;
+    const uint32_t rem = (uint32_t)min((size_t)kTcTile, (size_t)a.n - tb);
+    for (uint32_t p = t; p < rem; p += kTcThreads) {
+      uint32_t flag = 0;
+      const uint32_t u = a.keys[tb + p];
+      uint32_t b = tc_bucket<KIND>(u, sp, L, flag);
+      if constexpr (KIND == kRange)
+        if (flag & kTcLutFlag) b = range_search<5>(u, s_tbl, m);
+      atomicAdd(my + b * kTcRow, 1u);
+    }
+  }
+  if constexpr (SMALLM) flush();
+  __syncthreads();
+
+  // column c of H: warp w sums buckets w, w+8, w+16, w+24 over the 256 threads
+  for (uint32_t b = w; b < m; b += kTcThreads / 32) {
+    const uint32_t* row = s_cnt + b * kTcRow + lane;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += row[36 * k];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
+    if (lane == 0) a.H[(size_t)b * a.G + c] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = (atomicAdd(a.arrive, 1u) == a.G - 1u) ? 1u : 0u;
+  __syncthreads();
+  if (s_last == 0u) return;
+  __threadfence();
+
+  // last CTA: exclusive scan of H_row in place (Eq. 2), bucket offsets
+  const uint32_t len = m * a.G;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < len; base += kTcTile) {
+    uint32_t v[16];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t idx = base + 16u * t + i;
+      v[i] = idx < len ? __ldcg(a.H + idx) : 0u;
+      sum += v[i];
+    }
+    uint32_t total;
+    uint32_t run = carry + tc_block_scan(sum, s_warp, &total);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t idx = base + 16u * t + i;
+      if (idx < len) {
+        a.H[idx] = run;
+        if (a.offsets != nullptr && idx % a.G == 0u) a.offsets[idx / a.G] = run;
+      }
+      run += v[i];
+    }
+    carry += total;
+    __syncthreads();  // s_warp is rewritten by the next round
+  }
+  if (t == 0 && a.offsets != nullptr) a.offsets[m] = carry;
+}
+
+// ---------------------------------------------------------------------------
+// Post-scan.
+struct TcPostArgs {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  uint32_t n;
+  uint32_t tiles_per_cta;
+  uint32_t num_tiles;
+  uint32_t G;
+  const uint32_t* Gx;  // exclusive scan of row-vectorised H (m * G entries)
+  uint32_t* err;       // device status word
+  uint32_t tma;        // 1: full tiles arrive by tensor copies (inputs 16-byte aligned)
+  uint32_t lb, lw;     // lookup table: 2^lb cells, 2^lw copies (range buckets)
+  DevSpec sp;
+};
+
+// Dynamic shared memory (words), from a 1024-byte-aligned base: ring of
+// STAGES key slots (and value slots), counters R * 288, splitter table (32),
+// lookup table.  1 KB of slack for the alignment.
+template <int KIND, bool PAIRS, int STAGES>
+struct TcPostLayout {
+  static constexpr uint32_t T = kTcTile;
+  static constexpr uint32_t kRingWords = STAGES * T * (PAIRS ? 2 : 1);
+  static __host__ __device__ uint32_t cnt() { return kRingWords; }
+  static __host__ __device__ uint32_t tbl(uint32_t R) { return cnt() + R * kTcRow; }
+  static __host__ __device__ uint32_t lut(uint32_t R) { return tbl(R) + 32; }
+  static __host__ size_t bytes(uint32_t m, uint32_t lb, uint32_t lw) {
+    return 1024u + 4u * (size_t)(lut(tc_rows(m)) + tc_lut_words(KIND, lb, lw));
+  }
+};
+
+template <int KIND, bool PAIRS, int STAGES>
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_postscan_tc(const __grid_constant__ CUtensorMap tmk, const __grid_constant__ CUtensorMap tmv, TcPostArgs a) {
+  using Lay = TcPostLayout<KIND, PAIRS, STAGES>;
+  constexpr uint32_t T = Lay::T;
+  extern __shared__ __align__(16) uint32_t smem_raw[];
+  __shared__ __align__(8) uint64_t s_bar[STAGES];
+  __shared__ uint32_t s_pend[STAGES];  // 1 + index of the tile whose copy is in flight in the slot, 0 if none
+  __shared__ uint32_t s_run[kTcMaxM], s_delta[kTcMaxM], s_start[kTcMaxM];
+  __shared__ __align__(16) uint32_t s_warp[8];
+  const DevSpec& sp = a.sp;
+  const uint32_t m = sp.m, R = tc_rows(m);
+  const uint32_t sa = smem_addr(smem_raw);
+  uint32_t* base = smem_raw + (((1024u - (sa & 1023u)) & 1023u) >> 2);
+  uint32_t* ring_k = base;
+  uint32_t* ring_v = base + STAGES * T;
+  uint32_t* s_cnt = base + Lay::cnt();
+  uint32_t* s_tbl = base + Lay::tbl(R);
+  uint32_t* s_lut = base + Lay::lut(R);
+
+  const uint32_t t = threadIdx.x;
+  const TcLut L{s_lut, 32u - a.lb, a.lw, t & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u};
+  const uint32_t c = blockIdx.x;
+  const uint32_t t0 = c * a.tiles_per_cta;
+  const uint32_t t1 = min(t0 + a.tiles_per_cta, a.num_tiles);
+  const uint32_t ntiles = t1 > t0 ? t1 - t0 : 0u;
+  // the chunk is walked last tile first: the pre-scan read those last, so
+  // they are the ones still in L2
+  auto tile_of = [&](uint32_t j) { return t1 - 1u - j; };
+  auto is_full = [&](uint32_t j) { return (size_t)(tile_of(j) + 1u) * T <= a.n; };
+  const uint64_t pol = policy_evict_first();
+
+  auto issue = [&](uint32_t j) {  // thread 0: start the copies of tile j into its slot
+    if (!a.tma || j >= ntiles || !is_full(j)) return;
+    const uint32_t slot = j % STAGES;
+    const int y = (int)(tile_of(j) * (T / 32u));
+    mbar_arrive_expect_tx(s_bar + slot, T * 4u * (PAIRS ? 2u : 1u));
+    tma_tile_2d(ring_k + slot * T, &tmk, 0, y, s_bar + slot, pol);
+    if constexpr (PAIRS) tma_tile_2d(ring_v + slot * T, &tmv, 0, y, s_bar + slot, pol);
+    s_pend[slot] = j + 1u;
+  };
+
+  if (t == 0) {
+    for (int k = 0; k < STAGES; ++k) {
+      mbar_init(s_bar + k, 1);
+      s_pend[k] = 0u;
+    }
+    fence_mbar_init();
+  }
+  for (uint32_t i = t; i < R * kTcRow; i += kTcThreads) s_cnt[i] = 0u;
+  __syncthreads();
+  if (t == 0)
+    for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);  // inputs are not written by the pre-scan
+  tc_build_tables<KIND>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
+  pdl_wait();  // H scanned by the pre-scan grid
+  const uint32_t len = m * a.G;
+  for (uint32_t b = t; b < m; b += kTcThreads) {
+    const uint32_t e = b * a.G + c;
+    s_run[b] = (e + 1u < len) ? a.Gx[e + 1u] : a.n;  // end of bucket b's share of this chunk
+  }
+  __syncthreads();
+
+  uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)
+  uint32_t phase = 0;                          // bit k: parity of slot k's next completion
+
+  auto tile_body = [&](auto full_tag, uint32_t j) -> bool {
+    constexpr bool FULL = decltype(full_tag)::value;
+    const uint32_t tile = tile_of(j), slot = j % STAGES;
+    const size_t tb = (size_t)tile * T;
+    const uint32_t tile_n = FULL ? T : (uint32_t)((size_t)a.n - tb);
+    uint32_t* sk = ring_k + slot * T;
+    uint32_t* sv = ring_v + slot * T;
+    (void)sv;
+    bool ok = true;
+    if (FULL && a.tma) {
+      ok = mbar_wait(s_bar + slot, (phase >> slot) & 1u, a.err);
+      if (ok) phase ^= 1u << slot;
+    } else {
+      for (uint32_t p = t; p < tile_n; p += kTcThreads) {
+        sk[tc_swz(p)] = __ldcs(a.keys_in + tb + p);
+        if constexpr (PAIRS) sv[tc_swz(p)] = __ldcs(a.vals_in + tb + p);
+      }
+      __syncthreads();
+    }
+
+    // (A) this thread's 16 keys (and values), tile elements [16t, 16t+16)
+    uint32_t key[16], bk[16], pos[16];
+    uint32_t val[PAIRS ? 16 : 1];
+#pragma unroll
+    for (int j4 = 0; j4 < 4; ++j4) {
+      const uint4 v = *reinterpret_cast<const uint4*>(sk + tc_swz(16u * t + 4u * j4));
+      key[4 * j4 + 0] = v.x;
+      key[4 * j4 + 1] = v.y;
+      key[4 * j4 + 2] = v.z;
+      key[4 * j4 + 3] = v.w;
+      if constexpr (PAIRS) {
+        const uint4 x = *reinterpret_cast<const uint4*>(sv + tc_swz(16u * t + 4u * j4));
+        val[4 * j4 + 0] = x.x;
+        val[4 * j4 + 1] = x.y;
+        val[4 * j4 + 2] = x.z;
+        val[4 * j4 + 3] = x.w;
+      }
+    }
+    // (B) buckets
+    uint32_t flag = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+    if constexpr (KIND == kRange)
+      if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
+    // (C) rank of each key among the earlier keys of its bucket in this thread
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (FULL || 16u * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);
+    }
+    if (__syncthreads_or(!ok)) return false;  // (1) counts complete; the previous tile is written out
+    if (t == 0 && j > 0) {
+      // the previous tile's slot is free again: refill it
+      s_pend[(j - 1u) % STAGES] = 0u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(j - 1u + STAGES);
+    }
+    if (t == 0) s_pend[slot] = 0u;
+
+    // (D) one exclusive scan over the counters in (bucket, thread) order:
+    // thread r rakes counters [r*R, r*R + R)
+    {
+      uint4* seg = reinterpret_cast<uint4*>(s_cnt + tc_pad(t * R));
+      uint32_t sum = 0;
+      for (uint32_t g = 0; g < R / 4u; ++g) {
+        const uint4 v = seg[g];
+        sum += v.x + v.y + v.z + v.w;
+      }
+      uint32_t total;
+      uint32_t run = tc_block_scan(sum, s_warp, &total);  // contains barrier (2)
+      if (((t * R) & 255u) == 0u) {
+        const uint32_t b = (t * R) >> 8;
+        if (b < m) s_start[b] = run;  // counter (b, 0): where bucket b starts in the tile
+      }
+      // rows b >= m (R > m) stay zero: no key counts there, and nothing reads them
+      for (uint32_t g = 0; t * R < m * 256u && g < R / 4u; ++g) {
+        const uint4 v = seg[g];
+        uint4 o;
+        o.x = run;
+        run += v.x;
+        o.y = run;
+        run += v.y;
+        o.z = run;
+        run += v.z;
+        o.w = run;
+        run += v.w;
+        seg[g] = o;
+      }
+    }
+    __syncthreads();  // (3) scanned counters and bucket starts visible
+
+    // (E) per bucket: global position minus tile position
+    if (t < m) {
+      const uint32_t start = s_start[t];
+      const uint32_t end = (t + 1u < m) ? s_start[t + 1u] : tile_n;
+      const uint32_t g = s_run[t] - (end - start);
+      s_run[t] = g;
+      s_delta[t] = g - start;
+    }
+    // positions, then clear this thread's counters (rows < m; the scan wrote
+    // every one of them) for the next tile
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (FULL || 16u * t + i < tile_n) pos[i] += my[bk[i] * kTcRow];
+    }
+    for (uint32_t b = 0; b < m; ++b) my[b * kTcRow] = 0u;
+    // (F) permute the tile in place (every thread read its keys before (1))
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (FULL || 16u * t + i < tile_n) {
+        const uint32_t p = pos[i];
+        if (p < T) {
+          sk[tc_rswz(p)] = key[i];
+          if constexpr (PAIRS) sv[tc_rswz(p)] = val[i];
+        } else {
+          atomicOr(a.err, kDevErrBounds);
+        }
+      }
+    }
+    __syncthreads();  // (4)
+
+    // (G) consecutive threads write consecutive positions of each bucket run;
+    // a key's bucket is computed again from the key (cheaper here than
+    // storing it through shared memory)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t p = t + k * kTcThreads;
+      if (FULL || p < tile_n) {
+        const uint32_t q = tc_rswz(p);
+        const uint32_t u = sk[q];
+        uint32_t f = 0;
+        uint32_t b = tc_bucket<KIND>(u, sp, L, f);
+        if constexpr (KIND == kRange)
+          if (f & kTcLutFlag) b = range_search<5>(u, s_tbl, m);
+        const uint32_t g = s_delta[b] + p;
+        if (g < a.n) {
+          __stcs(a.keys_out + g, u);
+          if constexpr (PAIRS) __stcs(a.vals_out + g, sv[q]);
+        } else {
+          atomicOr(a.err, kDevErrBounds);
+        }
+      }
+    }
+    return true;
+  };
+
+  for (uint32_t j = 0; j < ntiles; ++j) {
+    const bool ok = is_full(j) ? tile_body(std::true_type{}, j) : tile_body(std::false_type{}, j);
+    if (!ok) {
+      // a copy never completed: drain the copies still in flight (bounded), then stop
+      if (t == 0)
+        for (int k = 0; k < STAGES; ++k)
+          if (s_pend[k] != 0u) mbar_drain(s_bar + k, (phase >> k) & 1u);
+      __syncthreads();
+      return;
+    }
+  }
+}
+
+}  // namespace ms

@@ -95,4 +95,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_
   return false;
 }
 
+// Wait bounded only by time (about one second), not given up early when
+// another wait has expired: used to drain copies still in flight before a CTA
+// that gave up exits.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t phase) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kMbarSpinLimit; ++i) {
+    if (mbar_try_wait(bar, phase)) return;
+    if ((i & 63u) == 63u && global_ns() - t0 > 1000000000ull) return;
+  }
+}
+
 }  // namespace ms

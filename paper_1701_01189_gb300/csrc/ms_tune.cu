@@ -16,16 +16,15 @@ std::mutex g_mu;
 bool g_set[kKinds][2][kNbits][kClasses] = {};
 Variant g_table[kKinds][2][kNbits][kClasses];
 
-// Measured on GB300 at n = 2^26 (all four identifiers): up to 8 buckets, warp
-// ballots with writes straight from registers win; beyond, peer tables with
-// block reordering.  Key-value pairs prefer the smaller 8 x 8 tile (two
-// arrays in flight per tile), except with 256 buckets (16 x 8).
+// Up to 32 buckets: per-thread bucket counters (ms_tc.cuh).  Beyond, peer
+// tables with block reordering; key-value pairs prefer the smaller 8 x 8 tile
+// (two arrays in flight per tile), except with 256 buckets (16 x 8).
 Variant default_variant(int nbits, int pairs) {
   Variant v;
-  if (nbits <= 3) {
-    v.rank = kRankBallot;
-    v.reorder = 0;
-    v.shape = pairs ? 2 : 0;
+  if (nbits <= 5) {
+    v.rank = kRankThread;
+    v.reorder = 1;
+    v.shape = 0;
   } else {
     v.rank = kRankTable;
     v.reorder = 1;
@@ -57,10 +56,10 @@ extern "C" int ms_tune_size_class(size_t n) { return n >= ((size_t)1 << 32) ? 3 
 
 extern "C" ms_status ms_tune_set(int kind, int pairs, int nbits, int sclass, int shape, int rank, int reorder) {
   if (kind < 0 || kind >= kKinds || pairs < 0 || pairs > 1 || nbits < 0 || nbits >= kNbits || sclass < 0 ||
-      sclass >= kClasses || shape < 0 || shape > 2 || rank < 0 || rank > 1 || reorder < 0 || reorder > 1)
+      sclass >= kClasses || shape < 0 || shape > 2 || rank < 0 || rank > 2 || reorder < 0 || reorder > 1)
     return MS_ERR_INVALID_ARG;
-  if (rank == kRankBallot && nbits > 5) return MS_ERR_INVALID_ARG;
-  if (reorder == 0 && (rank == kRankTable || nbits > 3)) return MS_ERR_INVALID_ARG;
+  if ((rank == kRankBallot || rank == kRankThread) && nbits > 5) return MS_ERR_INVALID_ARG;
+  if (reorder == 0 && (rank != kRankBallot || nbits > 3)) return MS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
   g_table[kind][pairs][nbits][sclass] = Variant{shape, rank, reorder};
   g_set[kind][pairs][nbits][sclass] = true;

@@ -22,6 +22,8 @@ def main(argv=None):
     ap.add_argument("--n-log2", type=int, default=26)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--variant", default=None,
+                    help="shape,rank,reorder of the kernel variant to run (see ms_tune_set); default: the tuned one")
     args = ap.parse_args(argv)
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -54,6 +56,13 @@ def main(argv=None):
     else:
         spec = ms.BucketSpec.delta_f32(args.m, float(np.float32(1000.0) / np.float32(args.m)))
     cs = spec.c()
+    if args.variant is not None and args.kind != "sort":
+        shape, rank, reorder = (int(x) for x in args.variant.split(","))
+        log2m = (args.m - 1).bit_length()
+        for pairs in (0, 1):
+            st = ms.ms_tune_set(spec.kind, pairs, log2m, ms.ms_tune_size_class(n), shape, rank, reorder)
+            if st != ms.MS_OK:
+                raise ms.MsError(st, "ms_tune_set")
 
     def run():
         if args.kind == "sort":
@@ -81,6 +90,8 @@ def main(argv=None):
     t = e0.elapsed_time(e1) / args.reps
     pre, scan, post, cnt = ms.ms_stage_times()
     desc = f"{args.kind} m={args.m if args.kind != 'sort' else 256} {'pairs' if args.pairs else 'keys'} n=2^{args.n_log2}"
+    if args.variant is not None:
+        desc += f" variant {args.variant}"
     line = f"{desc}: {t:.4f} ms per call = {n / t / 1e6:.1f} G elements/s"
     if cnt:
         line += f"; per multisplit: pre-scan {pre / cnt:.4f} ms, scan {scan / cnt:.4f} ms, post-scan {post / cnt:.4f} ms"

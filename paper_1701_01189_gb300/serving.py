@@ -13,9 +13,12 @@ sort of Section 7.1 to a stream of requests of mixed sizes, on one GPU:
 * Continuous batching: S launch slots, each with its own CUDA stream and its
   own dynamic batch plans.  Whenever a slot is idle, the requests that have
   arrived and fit are batched into it -- one persistent batched launch per
-  request class (each m; each of the four sort digits in turn) -- while the
-  batches of other slots are still running on the device.  A slot's
-  completion event marks its requests done and frees their memory.
+  request class (each m; each of the four sort digits in turn) for the small
+  requests, and the plain entry points on the slot's stream for requests of
+  at least `plain_min_elements` (they fill the GPU on their own, so batching
+  gains them nothing) -- while the batches of other slots are still running
+  on the device.  A slot's completion event marks its requests done and frees
+  their memory.
 * Reported: p50 / p99 latency (arrival to observed completion) and throughput
   in 1e9 elements per second, beside the same trace served one request at a
   time with the plain entry points.
@@ -129,7 +132,8 @@ class _Slot:
 
 class Service:
     def __init__(self, pool_keys, pool_vals, splitters: dict, arena_bytes: int = 16 * GIB, slots: int = 4,
-                 max_batch_segments: int = 256, max_batch_elements: int = 1 << 27):
+                 max_batch_segments: int = 256, max_batch_elements: int = 1 << 27,
+                 plain_min_elements: int = 1 << 18):
         import torch
 
         self.torch = torch
@@ -141,6 +145,7 @@ class Service:
         self.arena = torch.empty(arena_bytes // 4, dtype=torch.int32, device=self.dev)
         self.ring = RingArena(self.arena.numel())
         self.max_seg, self.max_el = max_batch_segments, max_batch_elements
+        self.plain_min = plain_min_elements
         self.slots = []
         for _ in range(slots):
             plans = {}
@@ -161,8 +166,12 @@ class Service:
         self.slots = []
 
     # ---------------------------------------------------------------- buffers of one request
+    def _plain(self, r: Request) -> bool:
+        return r.n >= self.plain_min
+
     def _words(self, r: Request) -> int:
-        return 2 * r.n + (2 * r.n if r.kind == "sort" else 0)  # out keys+vals (+ sort ping-pong)
+        # out keys + values (+ the ping-pong of a batched sort; a plain sort keeps its own)
+        return 2 * r.n + (2 * r.n if r.kind == "sort" and not self._plain(r) else 0)
 
     def out_views(self, r: Request):
         a = self.arena
@@ -176,8 +185,9 @@ class Service:
         vin = self.pv.data_ptr() + 4 * r.in_off
         ko = base + 4 * r.out_off
         vo = base + 4 * (r.out_off + r.n)
-        tk = base + 4 * (r.out_off + 2 * r.n) if r.kind == "sort" else None
-        tv = base + 4 * (r.out_off + 3 * r.n) if r.kind == "sort" else None
+        batched_sort = r.kind == "sort" and not self._plain(r)
+        tk = base + 4 * (r.out_off + 2 * r.n) if batched_sort else None
+        tv = base + 4 * (r.out_off + 3 * r.n) if batched_sort else None
         return kin, vin, ko, vo, tk, tv
 
     # ---------------------------------------------------------------- one batch on one slot
@@ -186,6 +196,14 @@ class Service:
         sptr = slot.stream.cuda_stream
         groups = {}
         for r in batch:
+            if self._plain(r):
+                kin, vin, ko, vo, _, _ = self._ptrs(r)
+                if r.kind == "multisplit":
+                    st = B.ms_multisplit_pairs(kin, vin, r.n, self.specs[r.m].c(), ko, vo, None, sptr)
+                else:
+                    st = B.ms_radix_sort(kin, vin, r.n, 0, 32, ko, vo, sptr)
+                B._check(st, "plain")
+                continue
             groups.setdefault((r.kind, r.m), []).append(r)
         for (kind, m), rs in groups.items():
             if kind == "multisplit":

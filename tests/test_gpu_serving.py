@@ -22,7 +22,7 @@ def test_served_results_equal_alone():
     spl = {m: to_dev(synthetic.range_splitters(m, m)) for m in (8, 32, 256)}
     trace = serving.make_trace(3000, 0.15, 5, pool=pool, n_lo=6, n_hi=18)
     svc = serving.Service(pk, pv, spl, arena_bytes=64 << 20, slots=3, max_batch_segments=64,
-                          max_batch_elements=1 << 21)
+                          max_batch_elements=1 << 21, plain_min_elements=1 << 15)
     got = {}
 
     def keep(r):  # called when r's results are ready, before its memory is reused
@@ -47,6 +47,7 @@ def test_served_results_equal_alone():
         np.testing.assert_array_equal(got_v, to_host(ev))
         checked += 1
     assert checked == len(trace)
+    assert any(r.n >= 1 << 15 for r in trace) and any(r.n < 1 << 15 for r in trace)  # both paths ran
     svc.close()
 
 

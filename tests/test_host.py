@@ -113,15 +113,18 @@ def test_tuning_table_validation_and_defaults(lib):
     ms.ms_tune_reset()
     assert ms.ms_tune_size_class(0) == 0 and ms.ms_tune_size_class(1 << 16) == 1
     assert ms.ms_tune_size_class((1 << 24) - 1) == 2 and ms.ms_tune_size_class(1 << 28) == 3
-    assert ms.ms_tune_get(ms.RANGE_U32, 0, 1, 3) == (0, 0, 0)  # m = 2: ballots, direct writes
+    assert ms.ms_tune_get(ms.RANGE_U32, 0, 1, 3) == (0, 2, 1)  # m = 2: per-thread counters
     assert ms.ms_tune_get(ms.RANGE_U32, 1, 8, 3) == (1, 1, 1)  # m = 256 pairs: peer tables, 16 x 8
-    assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (0, 1, 1)  # m = 32: peer tables
+    assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (0, 2, 1)  # m = 32: per-thread counters
+    assert ms.ms_tune_get(ms.MOD, 1, 6, 3) == (2, 1, 1)  # m = 64 pairs: peer tables, 8 x 8
     assert ms.ms_tune_set(ms.MOD, 0, 6, 3, 1, 0, 1) == ms.MS_ERR_INVALID_ARG  # ballots need log2 m <= 5
     assert ms.ms_tune_set(ms.MOD, 0, 4, 3, 1, 0, 0) == ms.MS_ERR_INVALID_ARG  # direct writes need log2 m <= 3
     assert ms.ms_tune_set(ms.MOD, 0, 5, 3, 1, 1, 0) == ms.MS_ERR_INVALID_ARG  # tables always reorder
     assert ms.ms_tune_set(ms.MOD, 0, 5, 3, 3, 1, 1) == ms.MS_ERR_INVALID_ARG  # no shape 3
     assert ms.ms_tune_set(4, 0, 5, 3, 0, 1, 1) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_tune_set(ms.MOD, 0, 6, 3, 0, 2, 1) == ms.MS_ERR_INVALID_ARG  # counters need log2 m <= 5
+    assert ms.ms_tune_set(ms.MOD, 0, 5, 3, 0, 2, 0) == ms.MS_ERR_INVALID_ARG  # counters always reorder
     assert ms.ms_tune_set(ms.MOD, 0, 5, 3, 2, 1, 1) == ms.MS_OK
     assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (2, 1, 1)
     ms.ms_tune_reset()
-    assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (0, 1, 1)
+    assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (0, 2, 1)
