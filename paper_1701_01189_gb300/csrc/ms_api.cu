@@ -41,6 +41,11 @@ static ms_status current_ctx(DeviceCtx** out) {
     if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return MS_ERR_CUDA;
     uint64_t keep = UINT64_MAX;  // keep freed scratch cached in the pool
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // scratch freed on one stream is not handed to another by making the
+    // second wait on the first: concurrent calls on different streams stay
+    // concurrent (the pool grows instead)
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     uint32_t* d_err = nullptr;
     if (cudaMalloc(&d_err, sizeof(uint32_t)) != cudaSuccess) {
       cudaMemPoolDestroy(pool);

@@ -237,6 +237,8 @@ __global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArg
 
 }  // namespace ms
 
+#include "ms_batch_tc.cuh"
+
 using namespace ms;
 
 struct ms_batch_plan {
@@ -250,6 +252,7 @@ struct ms_batch_plan {
   uint32_t num_segments = 0, n_items = 0;
   uint32_t grid = 0;
   size_t smem = 0;
+  uint32_t lb = 0, lw = 0;  // m <= 32: splitter lookup table of k_batch_tc
   DevSeg* d_segs = nullptr;
   uint2* d_items = nullptr;  // [0] = (n_hist, n_items), then the items
   uint32_t* d_H = nullptr;
@@ -267,6 +270,19 @@ namespace ms {
 
 template <int KIND, bool PAIRS>
 static cudaError_t batch_setup(ms_batch_plan& p, int sm_count) {
+  if (p.sp.m <= kTcMaxM) {
+    auto k = k_batch_tc<KIND, PAIRS>;
+    p.lb = 9;
+    p.lw = (PAIRS && p.sp.m > 16) ? 1u : 2u;
+    p.smem = BatchTcLayout<KIND, PAIRS>::bytes(p.sp.m, p.lb, p.lw);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kTcThreads, p.smem);
+    if (e != cudaSuccess) return e;
+    p.grid = (uint32_t)std::max(1, nb) * (uint32_t)sm_count;
+    return cudaSuccess;
+  }
   auto k = k_batch<KIND, PAIRS>;
   p.smem = BatchLayout<KIND, PAIRS>::bytes(p.sp.lut_bits);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
@@ -289,7 +305,10 @@ static cudaError_t batch_launch(const ms_batch_plan& p, cudaStream_t s) {
   a.ticket = p.d_flags + 2 * p.max_segments;
   a.err = p.d_err;
   a.sp = p.sp;
-  k_batch<KIND, PAIRS><<<p.grid, kBatchNW * 32, p.smem, s>>>(a);
+  if (p.sp.m <= kTcMaxM)
+    k_batch_tc<KIND, PAIRS><<<p.grid, kTcThreads, p.smem, s>>>(a, p.lb, p.lw);
+  else
+    k_batch<KIND, PAIRS><<<p.grid, kBatchNW * 32, p.smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,290 @@
+// ms_batch_tc.cuh -- the persistent batched multisplit (ms_batch.cu) for up to
+// 32 buckets, solving each tile with the per-thread bucket counters of
+// ms_tc.cuh.
+//
+// Same work list and protocol as k_batch: histogram items of multi-tile
+// segments first (tile histogram -> column of the segment's H; the CTA that
+// finishes a segment's last histogram scans its H and raises the ready flag),
+// then one post-scan item per tile.  Differences: a histogram item only
+// counts (one shared atomic per key, no ranks), and every CTA copies the next
+// item's tile into the other of two shared-memory slots with asynchronous
+// 4-byte copies (any alignment) while it works on the current one.  Items
+// are taken by ticket and the next ticket is taken before the current item is
+// done; a waiting post-scan item only waits for histogram items, whose
+// tickets are all smaller and whose holders never wait, so every wait ends.
+#pragma once
+
+#include "ms_tc.cuh"
+
+namespace ms {
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Dynamic shared memory (words): two slots (keys T, then values T for pairs),
+// counters R * 288, bucket bytes (T), splitter table 32, lookup table.
+template <int KIND, bool PAIRS>
+struct BatchTcLayout {
+  static constexpr uint32_t T = kTcTile;
+  static constexpr uint32_t kSlotWords = T * (PAIRS ? 2 : 1);
+  static __host__ __device__ uint32_t cnt() { return 2 * kSlotWords; }
+  static __host__ __device__ uint32_t bkt(uint32_t R) { return cnt() + R * kTcRow; }
+  static __host__ __device__ uint32_t tbl(uint32_t R) { return bkt(R) + T / 4; }
+  static __host__ __device__ uint32_t lut(uint32_t R) { return tbl(R) + 32; }
+  static __host__ size_t bytes(uint32_t m, uint32_t lb, uint32_t lw) {
+    return 4u * (size_t)(lut(tc_rows(m)) + tc_lut_words(KIND, lb, lw));
+  }
+};
+
+template <int KIND, bool PAIRS>
+__global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_t lb, uint32_t lw) {
+  using Lay = BatchTcLayout<KIND, PAIRS>;
+  constexpr uint32_t T = Lay::T;
+  constexpr uint32_t SW = Lay::kSlotWords;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_next, s_flag;
+  __shared__ uint32_t s_delta[kTcMaxM], s_start[kTcMaxM];
+  __shared__ __align__(16) uint32_t s_warp[8];
+  const DevSpec& sp = a.sp;
+  const uint32_t m = sp.m, R = tc_rows(m);
+  uint32_t* s_cnt = smem + Lay::cnt();
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(smem + Lay::bkt(R));
+  uint32_t* s_tbl = smem + Lay::tbl(R);
+  uint32_t* s_lut = smem + Lay::lut(R);
+  const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
+  const TcLut L{s_lut, 32u - lb, lw, lane & ((1u << lw) - 1u), (1u << (32u - lb)) - 1u};
+  uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)
+
+  for (uint32_t i = t; i < R * kTcRow; i += kTcThreads) s_cnt[i] = 0u;
+  tc_build_tables<KIND>(sp, lb, lw, s_tbl, s_lut);  // ends with a barrier
+  const uint2 counts = a.items[0];  // read from memory so a captured graph follows later updates
+  const uint32_t n_hist = counts.x, n_items = counts.y;
+
+  // all threads: copy item `it`'s tile (keys; values for a key-value
+  // post-scan) into `slot`, laid out as ms_tc.cuh's swizzled tiles; one
+  // commit group per call, empty or not
+  auto fetch = [&](uint32_t it, uint32_t slot) {
+    if (it < n_items) {
+      const uint2 item = a.items[1 + it];
+      const DevSeg sg = a.segs[item.x];
+      const size_t tb = (size_t)item.y * T;
+      const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
+      uint32_t* sk = smem + slot * SW;
+      const bool vals = PAIRS && it >= n_hist;
+      for (uint32_t p = t; p < tile_n; p += kTcThreads) {
+        cp_async4(sk + tc_swz(p), sg.kin + tb + p);
+        if (vals) cp_async4(sk + T + tc_swz(p), sg.vin + tb + p);
+      }
+    }
+    cp_async_commit();
+  };
+
+  if (t == 0) s_next = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  uint32_t cur = s_next;
+  uint32_t slot = 0;
+  fetch(cur, 0);
+
+  while (cur < n_items) {
+    __syncthreads();  // the other slot's last item is written out; everyone read s_next
+    if (t == 0) s_next = atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const uint32_t nxt = s_next;
+    fetch(nxt, slot ^ 1u);
+    cp_async_wait<1>();  // this thread's copies of the current item landed
+    __syncthreads();     // everyone's
+
+    const uint2 item = a.items[1 + cur];
+    const uint32_t seg = item.x, tile = item.y;
+    const DevSeg sg = a.segs[seg];
+    const size_t tb = (size_t)tile * T;
+    const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
+    uint32_t* sk = smem + slot * SW;
+    uint32_t* sv = sk + T;
+    (void)sv;
+
+    uint32_t key[16], bk[16];
+#pragma unroll
+    for (int j4 = 0; j4 < 4; ++j4) {
+      const uint4 v = *reinterpret_cast<const uint4*>(sk + tc_swz(16u * t + 4u * j4));
+      key[4 * j4 + 0] = v.x;
+      key[4 * j4 + 1] = v.y;
+      key[4 * j4 + 2] = v.z;
+      key[4 * j4 + 3] = v.w;
+    }
+    uint32_t flag = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+    if constexpr (KIND == kRange)
+      if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
+
+    if (cur < n_hist) {
+      // (A) tile histogram -> column `tile` of the segment's H
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (16u * t + i < tile_n) atomicAdd(my + bk[i] * kTcRow, 1u);
+      __syncthreads();
+      for (uint32_t b = w; b < m; b += kTcThreads / 32) {
+        uint32_t* row = s_cnt + b * kTcRow + lane;
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          s += row[36 * k];
+          row[36 * k] = 0u;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
+        if (lane == 0) a.H[sg.hoff + b * sg.L + tile] = s;
+      }
+      __threadfence();
+      __syncthreads();
+      if (t == 0) s_flag = (atomicAdd(a.done + seg, 1u) == sg.L - 1u) ? 1u : 0u;
+      __syncthreads();
+      if (s_flag) {
+        // last histogram of the segment: exclusive scan of its H (m * L
+        // words, bucket-major), bucket offsets, then the ready flag
+        __threadfence();
+        const uint32_t len = m * sg.L;
+        uint32_t* Hs = a.H + sg.hoff;
+        uint32_t carry = 0;
+        for (uint32_t base = 0; base < len; base += kTcTile) {
+          uint32_t v[16];
+          uint32_t sum = 0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint32_t idx = base + 16u * t + i;
+            v[i] = idx < len ? __ldcg(Hs + idx) : 0u;
+            sum += v[i];
+          }
+          uint32_t total;
+          uint32_t run = carry + tc_block_scan(sum, s_warp, &total);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint32_t idx = base + 16u * t + i;
+            if (idx < len) {
+              Hs[idx] = run;
+              if (sg.offsets != nullptr && idx % sg.L == 0u) sg.offsets[idx / sg.L] = run;
+            }
+            run += v[i];
+          }
+          carry += total;
+          __syncthreads();  // s_warp is rewritten by the next round
+        }
+        if (sg.offsets != nullptr && t == 0) sg.offsets[m] = carry;
+        __threadfence();
+        __syncthreads();
+        if (t == 0) st_release_u32(a.ready + seg, 1u);
+      }
+    } else {
+      // (B) post-scan of one tile
+      uint32_t val[PAIRS ? 16 : 1], pos[16];
+      if constexpr (PAIRS) {
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const uint4 x = *reinterpret_cast<const uint4*>(sv + tc_swz(16u * t + 4u * j4));
+          val[4 * j4 + 0] = x.x;
+          val[4 * j4 + 1] = x.y;
+          val[4 * j4 + 2] = x.z;
+          val[4 * j4 + 3] = x.w;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (16u * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);
+      __syncthreads();
+      {
+        uint4* segc = reinterpret_cast<uint4*>(s_cnt + tc_pad(t * R));
+        uint32_t sum = 0;
+        for (uint32_t g = 0; g < R / 4u; ++g) {
+          const uint4 v = segc[g];
+          sum += v.x + v.y + v.z + v.w;
+        }
+        uint32_t total;
+        uint32_t run = tc_block_scan(sum, s_warp, &total);
+        if (((t * R) & 255u) == 0u) {
+          const uint32_t b = (t * R) >> 8;
+          if (b < m) s_start[b] = run;
+        }
+        for (uint32_t g = 0; t * R < m * 256u && g < R / 4u; ++g) {
+          const uint4 v = segc[g];
+          uint4 o;
+          o.x = run;
+          run += v.x;
+          o.y = run;
+          run += v.y;
+          o.z = run;
+          run += v.z;
+          o.w = run;
+          run += v.w;
+          segc[g] = o;
+        }
+      }
+      __syncthreads();
+      // global base of each bucket for this tile
+      if (t < m) {
+        const uint32_t start = s_start[t];
+        if (sg.L == 1u) {
+          s_delta[t] = 0u;  // the tile is the segment
+          if (sg.offsets != nullptr) {
+            sg.offsets[t] = start;
+            if (t == 0) sg.offsets[m] = tile_n;
+          }
+        } else {
+          uint32_t spins = 0;
+          while (ld_acquire_u32(a.ready + seg) == 0u) {
+            // give up at the bound, or at once when another wait has already given up
+            if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
+              atomicOr(a.err, kDevErrTimeout);
+              break;
+            }
+            __nanosleep(spins < 64 ? 64 : 512);
+          }
+          s_delta[t] = __ldcg(a.H + sg.hoff + t * sg.L + tile) - start;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (16u * t + i < tile_n) pos[i] += my[bk[i] * kTcRow];
+      for (uint32_t b = 0; b < m; ++b) my[b * kTcRow] = 0u;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (16u * t + i < tile_n) {
+          const uint32_t p = pos[i];
+          if (p < T) {
+            sk[tc_rswz(p)] = key[i];
+            if constexpr (PAIRS) sv[tc_rswz(p)] = val[i];
+            s_bkt[tc_rswz(p)] = (uint8_t)bk[i];
+          } else {
+            atomicOr(a.err, kDevErrBounds);
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t p = t + k * kTcThreads;
+        if (p < tile_n) {
+          const uint32_t q = tc_rswz(p);
+          const uint32_t g = s_delta[s_bkt[q]] + p;
+          if (g < sg.n) {
+            __stcs(sg.kout + g, sk[q]);
+            if constexpr (PAIRS) __stcs(sg.vout + g, sv[q]);
+          } else {
+            atomicOr(a.err, kDevErrBounds);
+          }
+        }
+      }
+    }
+    cur = nxt;
+    slot ^= 1u;
+  }
+  cp_async_wait<0>();  // nothing may be in flight into shared memory at exit
+}
+
+}  // namespace ms

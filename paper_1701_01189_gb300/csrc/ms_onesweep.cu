@@ -33,6 +33,7 @@ constexpr uint32_t kOsAggregate = 1u << 30;
 constexpr uint32_t kOsPrefix = 2u << 30;
 constexpr uint32_t kOsValue = (1u << 30) - 1u;
 constexpr int kOsNW = 8, kOsItems = 16;
+constexpr int kOsLookback = 8;  // predecessors read per look-back step
 constexpr uint32_t kOsTile = kOsNW * 32 * kOsItems;  // 4096 keys
 constexpr int kHistNW = 8, kHistItems = 16;
 
@@ -121,8 +122,9 @@ struct OsLayout {
 
 // One digit pass, persistent: every CTA takes tiles by ticket (so every
 // earlier tile belongs to a CTA that already started, and the look-back below
-// always ends), and while it works on one tile the copy of its next tile is in
-// flight into the other slot.
+// always ends); once a tile's prefixes are published, the CTA takes its next
+// ticket and copies that tile into the other slot while it reorders and
+// writes the current one.
 template <bool PAIRS>
 __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(OnesweepArgs a) {
   using Lay = OsLayout<PAIRS>;
@@ -181,13 +183,6 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
     const uint32_t slot = k & 1u;
     const uint32_t tile = s_tile[slot];
     if (tile >= L) break;
-    if (threadIdx.x == 0) {
-      // the other slot was emptied before the last barrier: prefetch the next tile
-      const uint32_t nx = atomicAdd(a.ticket, 1u);
-      s_tile[slot ^ 1u] = nx;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(nx, slot ^ 1u);
-    }
     uint32_t* sk = smem + slot * Lay::kSlotWords;
     uint32_t* sv = sk + T;
     (void)sv;
@@ -239,26 +234,48 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
         st_relaxed_u32(st, kOsPrefix | hist);
       } else {
         st_relaxed_u32(st, kOsAggregate | hist);
-        for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
-          const uint32_t* q = a.status + (size_t)p * 256 + d;
-          uint32_t v = ld_relaxed_u32(q);
-          uint32_t spins = 0;
-          while ((v & ~kOsValue) == 0u) {
-            // give up at the bound, or at once when another wait has already given up
-            if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
-              atomicOr(a.err, kDevErrTimeout);
-              v = kOsPrefix;
-              break;
+        // Walk back 8 predecessors per step, their status words read at once
+        // (hundreds of tiles are in flight, most of them with only an
+        // aggregate published, so a walk is many tiles long); before tile 0
+        // counts as an inclusive prefix of 0.
+        bool found = false;
+        for (int64_t p0 = (int64_t)tile - 1; !found; p0 -= kOsLookback) {
+          uint32_t v[kOsLookback];
+#pragma unroll
+          for (int j = 0; j < kOsLookback; ++j)
+            v[j] = (p0 - j >= 0) ? ld_relaxed_u32(a.status + (size_t)(p0 - j) * 256 + d) : kOsPrefix;
+#pragma unroll
+          for (int j = 0; j < kOsLookback; ++j) {
+            if (found) continue;
+            const uint32_t* q = a.status + (size_t)(p0 - j) * 256 + d;
+            uint32_t spins = 0;
+            while ((v[j] & ~kOsValue) == 0u) {
+              // give up at the bound, or at once when another wait has already given up
+              if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
+                atomicOr(a.err, kDevErrTimeout);
+                v[j] = kOsPrefix;
+                break;
+              }
+              __nanosleep(spins < 64 ? 32 : 256);
+              v[j] = ld_relaxed_u32(q);
             }
-            __nanosleep(spins < 64 ? 32 : 256);
-            v = ld_relaxed_u32(q);
+            excl += v[j] & kOsValue;
+            if ((v[j] & ~kOsValue) == kOsPrefix) found = true;
           }
-          excl += v & kOsValue;
-          if ((v & ~kOsValue) == kOsPrefix) break;
         }
         st_relaxed_u32(st, kOsPrefix | ((excl + hist) & kOsValue));
       }
       s_delta[d] = s_goff[d] + excl - tstart;
+    }
+    if (threadIdx.x == 0) {
+      // This tile's prefixes are published: take the next ticket now (a
+      // ticket taken earlier would sit unstarted while later tiles wait on
+      // it) and start its copy into the other slot, emptied before the last
+      // barrier, to overlap the reorder and writes below.
+      const uint32_t nx = atomicAdd(a.ticket, 1u);
+      s_tile[slot ^ 1u] = nx;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(nx, slot ^ 1u);
     }
     // this thread's keys (and values) into registers before the in-place permutation
     uint32_t kr[kOsItems];

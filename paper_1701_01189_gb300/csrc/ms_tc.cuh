@@ -372,14 +372,15 @@ struct TcPostArgs {
 };
 
 // Dynamic shared memory (words), from a 1024-byte-aligned base: ring of
-// STAGES key slots (and value slots), counters R * 288, splitter table (32),
-// lookup table.  1 KB of slack for the alignment.
+// STAGES key slots (and value slots), counters R * 288, bucket bytes (T),
+// splitter table (32), lookup table.  1 KB of slack for the alignment.
 template <int KIND, bool PAIRS, int STAGES>
 struct TcPostLayout {
   static constexpr uint32_t T = kTcTile;
   static constexpr uint32_t kRingWords = STAGES * T * (PAIRS ? 2 : 1);
   static __host__ __device__ uint32_t cnt() { return kRingWords; }
-  static __host__ __device__ uint32_t tbl(uint32_t R) { return cnt() + R * kTcRow; }
+  static __host__ __device__ uint32_t bkt(uint32_t R) { return cnt() + R * kTcRow; }
+  static __host__ __device__ uint32_t tbl(uint32_t R) { return bkt(R) + T / 4; }
   static __host__ __device__ uint32_t lut(uint32_t R) { return tbl(R) + 32; }
   static __host__ size_t bytes(uint32_t m, uint32_t lb, uint32_t lw) {
     return 1024u + 4u * (size_t)(lut(tc_rows(m)) + tc_lut_words(KIND, lb, lw));
@@ -403,6 +404,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   uint32_t* ring_k = base;
   uint32_t* ring_v = base + STAGES * T;
   uint32_t* s_cnt = base + Lay::cnt();
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(base + Lay::bkt(R));
   uint32_t* s_tbl = base + Lay::tbl(R);
   uint32_t* s_lut = base + Lay::lut(R);
 
@@ -564,6 +566,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         if (p < T) {
           sk[tc_rswz(p)] = key[i];
           if constexpr (PAIRS) sv[tc_rswz(p)] = val[i];
+          s_bkt[tc_rswz(p)] = (uint8_t)bk[i];
         } else {
           atomicOr(a.err, kDevErrBounds);
         }
@@ -571,22 +574,15 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     }
     __syncthreads();  // (4)
 
-    // (G) consecutive threads write consecutive positions of each bucket run;
-    // a key's bucket is computed again from the key (cheaper here than
-    // storing it through shared memory)
+    // (G) consecutive threads write consecutive positions of each bucket run
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const uint32_t p = t + k * kTcThreads;
       if (FULL || p < tile_n) {
         const uint32_t q = tc_rswz(p);
-        const uint32_t u = sk[q];
-        uint32_t f = 0;
-        uint32_t b = tc_bucket<KIND>(u, sp, L, f);
-        if constexpr (KIND == kRange)
-          if (f & kTcLutFlag) b = range_search<5>(u, s_tbl, m);
-        const uint32_t g = s_delta[b] + p;
+        const uint32_t g = s_delta[s_bkt[q]] + p;
         if (g < a.n) {
-          __stcs(a.keys_out + g, u);
+          __stcs(a.keys_out + g, sk[q]);
           if constexpr (PAIRS) __stcs(a.vals_out + g, sv[q]);
         } else {
           atomicOr(a.err, kDevErrBounds);
