@@ -288,7 +288,7 @@ def run_gpu(args, rank: int, world: int):
     post_bytes = args.steps * n * (n_keys_cases * 8 + n_pairs_cases * 16)
     achieved = post_bytes / (post_ms * 1e-3) / 1e9 if post_ms > 0 else None
     tr = profiled_traffic()
-    roofline = {"kernel": "k_postscan", "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+    roofline = {"kernel": "post-scan (k_postscan_tc for m <= 32, k_postscan beyond)", "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
                 "peak": peak, "peak_kind": f"{peak_kind} (copy bandwidth, burst)", "unit": "GB/s",
                 "frac": round(achieved / peak, 4) if achieved else None,
                 "traffic": (round(tr["bytes_per_launch_full"], 0) if tr else None),
@@ -304,7 +304,9 @@ def run_gpu(args, rank: int, world: int):
               "config": {"workload": WORKLOAD, "n": n, "cases": len(case_list),
                          "l2": "inputs (256 MB each) larger than L2; no flush",
                          "parallelism": "replicas" if world > 1 else "single"},
-              "gpu_launches": 3 * len(case_list) * args.steps,
+              # our kernels per multisplit: pre-scan (+ scan in its last CTA) and
+              # post-scan for m <= 32; pre-scan, look-back scan, post-scan beyond
+              "gpu_launches": sum(2 if c[3] <= 32 else 3 for c in case_list) * args.steps,
               "roofline": roofline, "sweep": per_case, "clocks": clk}
 
     if not args.no_e2e:
