@@ -15,7 +15,8 @@ compulsory-bytes HBM roofline (read once + write once: 8 B/key, 16 B/pair).
 ``roofline`` is the post-scan kernel (the dominant one), timed with CUDA events
 recorded by the library around each stage on the launching stream.  ``e2e``
 runs the same sweep from pinned host buffers with the host<->device copies in
-the timed region.  ``cpu_baseline`` times the CPU oracle on a bounded sample.
+the timed region.  ``cpu_baseline`` times the CPU oracle on a bounded sample.  ``extras`` holds
+the radix-sort, device-histogram, batched and serving configurations.
 
 ``--impl reference`` times the CPU oracle (the reference arm of this
 repository) on samples of the same workload.  With N > 1 (torchrun) every
@@ -429,6 +430,30 @@ def extras_gpu(args, ms, metrics, torch, dev):
         out[name] = {"ms": round(t, 4), ("gpairs_s" if pairs else "gkeys_s"): round(rate, 2),
                      "frac_compulsory_roofline": round(rate / comp, 4), "passes": passes}
         del keys, vals, ko, vo
+    torch.cuda.empty_cache()
+
+    # device histogram (Section 7.3): n = 2^26, Range (range splitters) and Even (float32 delta) buckets
+    n = 1 << 26
+    hk = dev_u32(synthetic.uniform_u32(n, 31))
+    hf = dev_u32(synthetic.uniform_f32_1000(n, 32))
+    counts = torch.empty(256, dtype=torch.int32, device=dev)
+    for m in (32, 256):
+        for name, keys, spec in ((f"histogram_range_m{m}", hk, ms.BucketSpec.range_u32(dev_u32(synthetic.range_splitters(m, 33)))),
+                                 (f"histogram_even_f32_m{m}", hf,
+                                  ms.BucketSpec.delta_f32(m, float(np.float32(1000.0) / np.float32(m))))):
+            cs = spec.c()
+            sptr = torch.cuda.current_stream().cuda_stream
+
+            def run_h():
+                st = ms.ms_histogram(keys.data_ptr(), n, cs, counts.data_ptr(), sptr)
+                if st != ms.MS_OK:
+                    raise ms.MsError(st, name)
+
+            t = _time(torch, run_h, reps=20)
+            rate = metrics.rate_g(n, t * 1e-3)
+            out[name] = {"ms": round(t, 4), "gkeys_s": round(rate, 2),
+                         "frac_read_roofline": round(rate / metrics.sol_rate_g(peak, 4), 4)}
+    del hk, hf, counts
     torch.cuda.empty_cache()
 
     # batched: 4096 segments, sizes floor(2^U), U ~ U(8, 20), key mod 32, pairs (value = index)

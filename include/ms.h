@@ -99,6 +99,16 @@ ms_status ms_multisplit_pairs(const uint32_t *keys_in, const uint32_t *vals_in, 
 ms_status ms_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, size_t n, int begin_bit,
                         int end_bit, uint32_t *keys_out, uint32_t *vals_out, void *stream);
 
+/* Device histogram (Section 7.3, "Even" and "Range" histograms built on the
+ * multisplit's pre-scan): counts[b] = number of keys whose bucket is b, for
+ * 0 <= b < m, under the same bucket identifiers (range splitters = Range,
+ * float32 delta buckets = Even).  keys: device, n words; counts: device, m
+ * words, overwritten.  Reads the keys once; no permutation is made.
+ * Errors: MS_ERR_INVALID_ARG for a bad spec, counts == NULL, keys == NULL
+ * with n > 0, or n >= 2^32. */
+ms_status ms_histogram(const uint32_t *keys, size_t n, const ms_bucket_spec *spec, uint32_t *counts,
+                       void *stream);
+
 /* Keys-only stable multisplit that allocates nothing (the paper has no
  * counterpart; this is a deployment variant of ms_multisplit_keys).  For
  * callers that must not allocate device memory during the call: work being

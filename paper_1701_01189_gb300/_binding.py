@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
         L.ms_multisplit_pairs.argtypes = [P, P, S, SP, P, P, P, P]
         L.ms_multisplit_keys_noalloc.argtypes = [P, S, SP, P, P, P]
         L.ms_radix_sort.argtypes = [P, P, S, I, I, P, P, P]
+        L.ms_histogram.argtypes = [P, S, SP, P, P]
         L.ms_device_status.argtypes = [P]
         L.ms_status_string.argtypes = [I]
         L.ms_status_string.restype = ctypes.c_char_p
@@ -103,7 +104,7 @@ def lib() -> ctypes.CDLL:
         L.ms_stage_timing.argtypes = [I]
         L.ms_stage_times.argtypes = [P, P, P, P]
         for f in ("ms_multisplit_keys", "ms_multisplit_pairs", "ms_multisplit_keys_noalloc", "ms_radix_sort",
-                  "ms_device_status",
+                  "ms_histogram", "ms_device_status",
                   "ms_stage_timing", "ms_stage_times"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -128,6 +129,10 @@ def ms_multisplit_keys_noalloc(keys_in: int, n: int, spec: "_Spec", keys_out: in
 def ms_radix_sort(keys_in: int, vals_in: int, n: int, begin_bit: int, end_bit: int, keys_out: int,
                   vals_out: int, stream: int) -> int:
     return lib().ms_radix_sort(keys_in, vals_in, n, begin_bit, end_bit, keys_out, vals_out, stream)
+
+
+def ms_histogram(keys: int, n: int, spec: "_Spec", counts: int, stream: int) -> int:
+    return lib().ms_histogram(keys, n, ctypes.byref(spec), counts, stream)
 
 
 def ms_device_status(stream: int) -> int:
@@ -294,6 +299,17 @@ def multisplit_keys(keys, spec: BucketSpec, keys_out=None, offsets=None, stream=
     _check(ms_multisplit_keys(keys.data_ptr(), n, cs, keys_out.data_ptr(), offsets.data_ptr(), _stream(stream)),
            "ms_multisplit_keys")
     return keys_out, offsets
+
+
+def histogram(keys, spec: BucketSpec, counts=None, stream=None):
+    """Device histogram (Section 7.3) of a 1-D CUDA tensor of 32-bit keys: counts[m]."""
+    import torch
+
+    keys = _u32_view(keys)
+    if counts is None:
+        counts = torch.empty(spec.m, dtype=torch.int32, device=keys.device)
+    _check(ms_histogram(keys.data_ptr(), keys.numel(), spec.c(), counts.data_ptr(), _stream(stream)), "ms_histogram")
+    return counts
 
 
 def multisplit_pairs(keys, vals, spec: BucketSpec, keys_out=None, vals_out=None, offsets=None, stream=None):

@@ -23,7 +23,7 @@ DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.
 
 
 def variants(log2m: int):
-    out = [(0, 2, 1)] if log2m <= 5 else []
+    out = [(0, 2, 1), (2, 2, 1)] if log2m <= 5 else []
     for shape in (0, 1, 2):
         out.append((shape, 1, 1))
         if log2m <= 5:

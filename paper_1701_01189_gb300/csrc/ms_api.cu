@@ -69,6 +69,16 @@ cudaError_t scratch_alloc(DeviceCtx& ctx, void** p, size_t bytes, cudaStream_t s
 
 cudaError_t scratch_free(void* p, cudaStream_t stream) { return p ? cudaFreeAsync(p, stream) : cudaSuccess; }
 
+__global__ void k_counts_from_offsets(const uint32_t* offsets, uint32_t* counts, uint32_t m) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < m) counts[b] = offsets[b + 1] - offsets[b];
+}
+
+cudaError_t launch_counts_from_offsets(const uint32_t* offsets, uint32_t* counts, uint32_t m, cudaStream_t s) {
+  k_counts_from_offsets<<<1, 256, 0, s>>>(offsets, counts, m);
+  return cudaGetLastError();
+}
+
 cudaError_t run_multisplit(const Call& c, DeviceCtx& ctx) {
   switch (c.kind) {
     case kRange: return run_multisplit_range(c, ctx);
@@ -203,6 +213,27 @@ extern "C" ms_status ms_multisplit_pairs(const uint32_t* keys_in, const uint32_t
                                          const ms_bucket_spec* spec, uint32_t* keys_out, uint32_t* vals_out,
                                          uint32_t* offsets, void* stream) {
   return multisplit_impl(keys_in, vals_in, n, spec, keys_out, vals_out, offsets, stream, true);
+}
+
+// Section 7.3: the device histogram is the multisplit's pre-scan alone --
+// per-chunk bucket counts and their scan -- with the bucket sizes as result.
+extern "C" ms_status ms_histogram(const uint32_t* keys, size_t n, const ms_bucket_spec* spec, uint32_t* counts,
+                                  void* stream) {
+  Call c;
+  std::memset(&c, 0, sizeof c);
+  ms_status st = make_devspec(spec, &c.sp, &c.kind);
+  if (st != MS_OK) return st;
+  if (n >= ((size_t)1 << 32) || counts == nullptr || (n > 0 && keys == nullptr)) return MS_ERR_INVALID_ARG;
+  DeviceCtx* ctx = nullptr;
+  st = current_ctx(&ctx);
+  if (st != MS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n == 0) return to_status(cudaMemsetAsync(counts, 0, (size_t)c.sp.m * 4, s));
+  c.keys_in = keys;
+  c.counts = counts;
+  c.n = (uint32_t)n;
+  c.stream = s;
+  return to_status(run_multisplit(c, *ctx));
 }
 
 // Section 7.1: LSD passes of multisplit with the radix-digit identifier

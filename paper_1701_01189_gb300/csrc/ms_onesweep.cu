@@ -33,7 +33,7 @@ constexpr uint32_t kOsAggregate = 1u << 30;
 constexpr uint32_t kOsPrefix = 2u << 30;
 constexpr uint32_t kOsValue = (1u << 30) - 1u;
 constexpr int kOsNW = 8, kOsItems = 16;
-constexpr int kOsLookback = 32;  // predecessors read per look-back step
+constexpr int kOsLookback = 8;  // predecessors read per look-back step
 constexpr uint32_t kOsTile = kOsNW * 32 * kOsItems;  // 4096 keys
 constexpr int kHistNW = 8, kHistItems = 16;
 
@@ -235,10 +235,10 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
       } else {
         st_relaxed_u32(st, kOsAggregate | hist);
         // Walk back kOsLookback predecessors per step, their status words
-        // read at once.  Hundreds of tiles are in flight; the newest inclusive
-        // prefix advances by about kOsLookback tiles per L2 round trip, which
-        // must keep up with the rate at which tiles start (measured: 8 was
-        // too few).  Before tile 0 counts as an inclusive prefix of 0.
+        // read at once: hundreds of tiles are in flight, most with only an
+        // aggregate published, so a walk spans many tiles (measured on GB300:
+        // 8 per step beats 1 and 32).  Before tile 0 counts as an inclusive
+        // prefix of 0.
         bool found = false;
         for (int64_t p0 = (int64_t)tile - 1; !found; p0 -= kOsLookback) {
           uint32_t v[kOsLookback];

@@ -28,6 +28,9 @@ static int setup_kernel(LaunchInfo& li, K kernel, int threads, size_t smem_max, 
   const int d = device & 63;
   if (!((li.ready >> d) & 1ull)) {
     if (smem_max > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    // these kernels read through TMA or no-allocate loads: give the SM's
+    // L1/shared storage to shared memory, so occupancy is not capped by the carveout
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     li.ready |= 1ull << d;
   }
   auto key = std::make_pair(d, smem);
@@ -88,9 +91,10 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   const uint32_t nscan = (len + kScanTile - 1) / kScanTile;
 
   // scratch: H (len words, 16-byte aligned) | scan status (nscan u64) | ticket
+  // | (histogram only) offsets
   const size_t h_bytes = ((size_t)len * 4 + 15) & ~(size_t)15;
   const size_t st_bytes = (size_t)nscan * 8;
-  const size_t bytes = h_bytes + st_bytes + 16;
+  const size_t bytes = h_bytes + st_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
   void* ws = nullptr;
   cudaError_t e = cudaSuccess;
   if (c.ws_fixed != nullptr) {
@@ -114,12 +118,17 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
     e = cudaGetLastError();
     trace_mark(slot, 1, c.stream);
   }
+  uint32_t* offsets = c.offsets;
+  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes + 16);
   if (e == cudaSuccess) {
-    ScanArgs sa{H, len, ch.G, c.offsets, m, status, ticket, ctx.d_err};
+    ScanArgs sa{H, len, ch.G, offsets, m, status, ticket, ctx.d_err};
     e = launch_scan_lookback(sa, c.stream);
     trace_mark(slot, 2, c.stream);
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && c.counts != nullptr) {
+    e = launch_counts_from_offsets(offsets, c.counts, m, c.stream);
+    trace_mark(slot, 3, c.stream);
+  } else if (e == cudaSuccess) {
     PostscanArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, c.sp, ch.K, ch.L, ch.G, H, ctx.d_err,
                     aligned, 1u};
     kpost<<<ch.G, THREADS, smem_post, c.stream>>>(qa);
@@ -159,7 +168,7 @@ static cudaError_t run_ms_ballot(const Call& c, DeviceCtx& ctx, const Variant& v
 template <int KIND>
 static cudaError_t run_ms_kind(const Call& c, DeviceCtx& ctx) {
   const Variant v = choose_variant(c);
-  if (v.rank == kRankThread && c.sp.m <= kTcMaxM) return run_tc<KIND>(c, ctx);
+  if (v.rank == kRankThread && c.sp.m <= kTcMaxM) return run_tc<KIND>(c, ctx, v.shape);
   if (v.rank == kRankBallot && c.sp.nbits <= 5) {
     switch (c.sp.nbits) {
       case 0: return run_ms_ballot<KIND, 0>(c, ctx, v);

@@ -33,14 +33,14 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // Tensor map of a uint32 array seen as rows of 32 words (floor(n / 32) rows),
-// box 32 x 128 (one 4096-key tile), 128-byte swizzle.  False if it cannot be
+// box 32 x (tile / 32) (one tile), 128-byte swizzle.  False if it cannot be
 // made (then the caller copies tiles with plain loads).
-inline bool make_tile_map(CUtensorMap* map, const uint32_t* base, uint32_t n) {
+inline bool make_tile_map(CUtensorMap* map, const uint32_t* base, uint32_t n, uint32_t tile) {
   auto enc = tensor_map_encoder();
-  if (enc == nullptr || n < kTcTile || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  if (enc == nullptr || n < tile || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
   const cuuint64_t dims[2] = {32, n / 32u};
   const cuuint64_t strides[1] = {128};
-  const cuuint32_t box[2] = {32, kTcTile / 32u};
+  const cuuint32_t box[2] = {32, tile / 32u};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(base), dims, strides, box,
                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -52,13 +52,13 @@ inline bool make_tile_map(CUtensorMap* map, const uint32_t* base, uint32_t n) {
 // last tiles of every chunk, about half of the 126 MB L2.
 constexpr size_t kTcL2KeepBytes = (size_t)64 << 20;
 
-template <int KIND, bool PAIRS, int STAGES>
+template <int KIND, bool PAIRS, int STAGES, int KPT>
 static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
-  constexpr uint32_t T = kTcTile;
+  constexpr uint32_t T = kTcThreads * KPT;  // post-scan tile; the pre-scan works in 4096-key tiles
   const bool small_m = c.sp.m <= 8;
   auto kpre = small_m ? k_prescan_tc<KIND, true> : k_prescan_tc<KIND, false>;
-  auto kpost = k_postscan_tc<KIND, PAIRS, STAGES>;
-  using Lay = TcPostLayout<KIND, PAIRS, STAGES>;
+  auto kpost = k_postscan_tc<KIND, PAIRS, STAGES, KPT>;
+  using Lay = TcPostLayout<KIND, PAIRS, STAGES, KPT>;
   const DevSpec& sp = c.sp;
   // splitter lookup tables: 1024 cells x 8 copies for the pre-scan; 512 cells
   // x 4 copies for the post-scan (x 2 for key-value pairs with more than 16
@@ -72,11 +72,14 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   setup_kernel(small_m ? li_pre_s : li_pre_l, kpre, kTcThreads, tc_prescan_smem<KIND>(kTcMaxM, pre_lb, pre_lw),
                smem_pre, ctx.device);
 
-  const Chunking ch = make_chunking(c.n, T, (uint32_t)(ctx.sm_count * nb_post));
+  // chunks are whole 4096-key pre-scan tiles; the post-scan walks them in its own tiles
+  const Chunking ch = make_chunking(c.n, kTcTile, (uint32_t)(ctx.sm_count * nb_post));
+  const uint32_t post_k = ch.K * (kTcTile / T);
+  const uint32_t post_l = (uint32_t)(((uint64_t)c.n + T - 1) / T);
   const uint32_t m = sp.m;
-  // scratch: H (m * G words) | arrival counter
+  // scratch: H (m * G words) | arrival counter | (histogram only) offsets
   const size_t h_bytes = ((size_t)m * ch.G * 4 + 15) & ~(size_t)15;
-  const size_t bytes = h_bytes + 16;
+  const size_t bytes = h_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
   void* ws = nullptr;
   cudaError_t e = cudaSuccess;
   if (c.ws_fixed != nullptr) {
@@ -94,22 +97,27 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   CUtensorMap tmk, tmv;
   std::memset(&tmk, 0, sizeof tmk);
   std::memset(&tmv, 0, sizeof tmv);
-  bool tma = make_tile_map(&tmk, c.keys_in, c.n);
-  if (tma && PAIRS) tma = make_tile_map(&tmv, c.vals_in, c.n);
+  bool tma = make_tile_map(&tmk, c.keys_in, c.n, T);
+  if (tma && PAIRS) tma = make_tile_map(&tmv, c.vals_in, c.n, T);
 
   // the last `keep` tiles of every chunk are read with evict_last
-  const size_t keep_tiles = kTcL2KeepBytes / ((size_t)T * 4);
+  const size_t keep_tiles = kTcL2KeepBytes / ((size_t)kTcTile * 4);
   const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
   const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
+  uint32_t* offsets = c.offsets;
+  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + 16);
   if (e == cudaSuccess) {
-    TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, arrive, c.offsets, pre_lb, pre_lw, sp};
+    TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, arrive, offsets, pre_lb, pre_lw, sp};
     kpre<<<ch.G, kTcThreads, smem_pre, c.stream>>>(pa);
     e = cudaGetLastError();
     trace_mark(slot, 1, c.stream);
     trace_mark(slot, 2, c.stream);  // the global scan runs inside the pre-scan
   }
-  if (e == cudaSuccess) {
-    TcPostArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, ch.K, ch.L, ch.G, H, ctx.d_err,
+  if (e == cudaSuccess && c.counts != nullptr) {
+    e = launch_counts_from_offsets(offsets, c.counts, m, c.stream);
+    trace_mark(slot, 3, c.stream);
+  } else if (e == cudaSuccess) {
+    TcPostArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, post_k, post_l, ch.G, H, ctx.d_err,
                   tma ? 1u : 0u, post_lb, post_lw, sp};
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof cfg);
@@ -129,10 +137,15 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   return e != cudaSuccess ? e : e2;
 }
 
+// Variant shape 2 selects 8 keys per thread, any other 16.
 template <int KIND>
-static cudaError_t run_tc(const Call& c, DeviceCtx& ctx) {
-  if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2>(c, ctx);
-  return run_tc_cfg<KIND, false, 2>(c, ctx);
+static cudaError_t run_tc(const Call& c, DeviceCtx& ctx, int shape) {
+  if (shape == 2) {
+    if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2, 8>(c, ctx);
+    return run_tc_cfg<KIND, false, 2, 8>(c, ctx);
+  }
+  if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2, 16>(c, ctx);
+  return run_tc_cfg<KIND, false, 2, 16>(c, ctx);
 }
 
 }  // namespace ms

@@ -374,9 +374,9 @@ struct TcPostArgs {
 // Dynamic shared memory (words), from a 1024-byte-aligned base: ring of
 // STAGES key slots (and value slots), counters R * 288, bucket bytes (T),
 // splitter table (32), lookup table.  1 KB of slack for the alignment.
-template <int KIND, bool PAIRS, int STAGES>
+template <int KIND, bool PAIRS, int STAGES, int KPT>
 struct TcPostLayout {
-  static constexpr uint32_t T = kTcTile;
+  static constexpr uint32_t T = kTcThreads * KPT;
   static constexpr uint32_t kRingWords = STAGES * T * (PAIRS ? 2 : 1);
   static __host__ __device__ uint32_t cnt() { return kRingWords; }
   static __host__ __device__ uint32_t bkt(uint32_t R) { return cnt() + R * kTcRow; }
@@ -387,10 +387,13 @@ struct TcPostLayout {
   }
 };
 
-template <int KIND, bool PAIRS, int STAGES>
-__global__ void __launch_bounds__(kTcThreads, 2)
+// KPT keys per thread (16, or 8: a 2048-key tile, half the registers per
+// thread, more CTAs per SM).
+template <int KIND, bool PAIRS, int STAGES, int KPT>
+__global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
     k_postscan_tc(const __grid_constant__ CUtensorMap tmk, const __grid_constant__ CUtensorMap tmv, TcPostArgs a) {
-  using Lay = TcPostLayout<KIND, PAIRS, STAGES>;
+  static_assert(KPT == 8 || KPT == 16, "8 or 16 keys per thread");
+  using Lay = TcPostLayout<KIND, PAIRS, STAGES, KPT>;
   constexpr uint32_t T = Lay::T;
   extern __shared__ __align__(16) uint32_t smem_raw[];
   __shared__ __align__(8) uint64_t s_bar[STAGES];
@@ -473,18 +476,18 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       __syncthreads();
     }
 
-    // (A) this thread's 16 keys (and values), tile elements [16t, 16t+16)
-    uint32_t key[16], bk[16], pos[16];
-    uint32_t val[PAIRS ? 16 : 1];
+    // (A) this thread's KPT keys (and values), tile elements [KPT t, KPT t + KPT)
+    uint32_t key[KPT], bk[KPT], pos[KPT];
+    uint32_t val[PAIRS ? KPT : 1];
 #pragma unroll
-    for (int j4 = 0; j4 < 4; ++j4) {
-      const uint4 v = *reinterpret_cast<const uint4*>(sk + tc_swz(16u * t + 4u * j4));
+    for (int j4 = 0; j4 < KPT / 4; ++j4) {
+      const uint4 v = *reinterpret_cast<const uint4*>(sk + tc_swz(KPT * t + 4u * j4));
       key[4 * j4 + 0] = v.x;
       key[4 * j4 + 1] = v.y;
       key[4 * j4 + 2] = v.z;
       key[4 * j4 + 3] = v.w;
       if constexpr (PAIRS) {
-        const uint4 x = *reinterpret_cast<const uint4*>(sv + tc_swz(16u * t + 4u * j4));
+        const uint4 x = *reinterpret_cast<const uint4*>(sv + tc_swz(KPT * t + 4u * j4));
         val[4 * j4 + 0] = x.x;
         val[4 * j4 + 1] = x.y;
         val[4 * j4 + 2] = x.z;
@@ -494,13 +497,13 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     // (B) buckets
     uint32_t flag = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+    for (int i = 0; i < KPT; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
     if constexpr (KIND == kRange)
-      if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
+      if (flag & kTcLutFlag) tc_fixup<KPT>(key, bk, L, s_tbl, m);
     // (C) rank of each key among the earlier keys of its bucket in this thread
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (FULL || 16u * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);
+    for (int i = 0; i < KPT; ++i) {
+      if (FULL || KPT * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);
     }
     if (__syncthreads_or(!ok)) return false;  // (1) counts complete; the previous tile is written out
     if (t == 0 && j > 0) {
@@ -554,14 +557,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     // positions, then clear this thread's counters (rows < m; the scan wrote
     // every one of them) for the next tile
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (FULL || 16u * t + i < tile_n) pos[i] += my[bk[i] * kTcRow];
+    for (int i = 0; i < KPT; ++i) {
+      if (FULL || KPT * t + i < tile_n) pos[i] += my[bk[i] * kTcRow];
     }
     for (uint32_t b = 0; b < m; ++b) my[b * kTcRow] = 0u;
     // (F) permute the tile in place (every thread read its keys before (1))
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (FULL || 16u * t + i < tile_n) {
+    for (int i = 0; i < KPT; ++i) {
+      if (FULL || KPT * t + i < tile_n) {
         const uint32_t p = pos[i];
         if (p < T) {
           sk[tc_rswz(p)] = key[i];
@@ -576,7 +579,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
     // (G) consecutive threads write consecutive positions of each bucket run
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < KPT; ++k) {
       const uint32_t p = t + k * kTcThreads;
       if (FULL || p < tile_n) {
         const uint32_t q = tc_rswz(p);

@@ -53,3 +53,23 @@ def test_every_variant_matches_oracle(kind, m):
             check_multisplit(keys, synthetic.index_values(n), case)
     finally:
         ms.ms_tune_reset()
+
+
+@pytest.mark.parametrize("shape", [0, 2], ids=["16-per-thread", "8-per-thread"])
+@pytest.mark.parametrize("m", [2, 8, 32])
+def test_counter_variants_many_tiles_per_chunk(m, shape):
+    """Per-thread-counter kernels at a size where every CTA walks many tiles
+    (and the last one is ragged), for both tile shapes."""
+    import paper_1701_01189_gb300 as ms
+
+    n = (1 << 22) + 77
+    case = make_case("range", m)
+    log2m = (m - 1).bit_length()
+    keys = synthetic.uniform_u32(n, 11)
+    try:
+        for pairs in (0, 1):
+            assert ms.ms_tune_set(case.kind, pairs, log2m, ms.ms_tune_size_class(n), shape, 2, 1) == ms.MS_OK
+        check_multisplit(keys, None, case)
+        check_multisplit(keys, synthetic.index_values(n), case)
+    finally:
+        ms.ms_tune_reset()

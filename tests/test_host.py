@@ -87,6 +87,10 @@ def test_bad_pointers_rejected(lib):
     assert ms.ms_radix_sort(0x1000, None, 16, 8, 4, 0x2000, None, None) == ms.MS_ERR_INVALID_ARG
     assert ms.ms_radix_sort(0x1000, None, 16, 0, 33, 0x2000, None, None) == ms.MS_ERR_INVALID_ARG
     assert ms.ms_radix_sort(0x1000, 0x3000, 16, 0, 32, 0x2000, None, None) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_histogram(0x1000, 16, good, None, None) == ms.MS_ERR_INVALID_ARG  # no counts
+    assert ms.ms_histogram(None, 16, good, 0x2000, None) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_histogram(0x1000, 1 << 32, good, 0x2000, None) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_histogram(0x1000, 16, BAD_SPECS[0], 0x2000, None) == ms.MS_ERR_INVALID_ARG
 
 
 def test_speed_of_light_model_matches_paper():
