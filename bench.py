@@ -16,7 +16,8 @@ compulsory-bytes HBM roofline (read once + write once: 8 B/key, 16 B/pair).
 recorded by the library around each stage on the launching stream.  ``e2e``
 runs the same sweep from pinned host buffers with the host<->device copies in
 the timed region.  ``cpu_baseline`` times the CPU oracle on a bounded sample.  ``extras`` holds
-the radix-sort, device-histogram, batched and serving configurations.
+the radix-sort, device-histogram, Section 6.4 distribution (uniform,
+0.25-uniform, binomial at m = 256), batched and serving configurations.
 
 ``--impl reference`` times the CPU oracle (the reference arm of this
 repository) on samples of the same workload.  With N > 1 (torchrun) every
@@ -454,6 +455,40 @@ def extras_gpu(args, ms, metrics, torch, dev):
             out[name] = {"ms": round(t, 4), "gkeys_s": round(rate, 2),
                          "frac_read_roofline": round(rate / metrics.sol_rate_g(peak, 4), 4)}
     del hk, hf, counts
+    torch.cuda.empty_cache()
+
+    # Section 6.4 / Table 6: delta buckets, m = 256, n = 2^25, uniform vs 0.25-uniform vs binomial B(255, 0.5)
+    n = 1 << 25
+    m = 256
+    delta = float(np.float32(1000.0) / np.float32(m))
+    spec = ms.BucketSpec.delta_f32(m, delta).c()
+    vals = dev_u32(synthetic.index_values(n))
+    ko, vo = torch.empty_like(vals), torch.empty_like(vals)
+    offs = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    sptr = torch.cuda.current_stream().cuda_stream
+    dist_rates = {}
+    for dname, gen in (("uniform", lambda: synthetic.uniform_f32_1000(n, 41)),
+                       ("0.25-uniform", lambda: synthetic.alpha_uniform_f32(n, m, delta, 0.25, 42)),
+                       ("binomial", lambda: synthetic.binomial_f32(n, m, delta, 43))):
+        keys = dev_u32(gen())
+        for pairs in (False, True):
+            def run_d():
+                if pairs:
+                    st = ms.ms_multisplit_pairs(keys.data_ptr(), vals.data_ptr(), n, spec, ko.data_ptr(),
+                                                vo.data_ptr(), offs.data_ptr(), sptr)
+                else:
+                    st = ms.ms_multisplit_keys(keys.data_ptr(), n, spec, ko.data_ptr(), offs.data_ptr(), sptr)
+                if st != ms.MS_OK:
+                    raise ms.MsError(st, dname)
+
+            t = _time(torch, run_d, reps=10)
+            dist_rates[(dname, pairs)] = metrics.rate_g(n, t * 1e-3)
+        del keys
+    for (dname, pairs), rate in dist_rates.items():
+        out[f"dist_delta_m256_{dname}_{'pairs' if pairs else 'keys'}"] = {
+            ("gpairs_s" if pairs else "gkeys_s"): round(rate, 2),
+            "speedup_vs_uniform": round(rate / dist_rates[("uniform", pairs)], 3)}
+    del vals, ko, vo, offs
     torch.cuda.empty_cache()
 
     # batched: 4096 segments, sizes floor(2^U), U ~ U(8, 20), key mod 32, pairs (value = index)

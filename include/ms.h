@@ -122,9 +122,9 @@ ms_status ms_histogram(const uint32_t *keys, size_t n, const ms_bucket_spec *spe
  *     capture.  It allocates nothing.
  *   - All calls share the array: calls that overlap on the GPU race and
  *     corrupt each other's results; serialize them (one stream, or events).
- *   - The scratch must hold 4*m*G + 8*ceil(m*G/4096) + 16 bytes (G = CTAs of
- *     the launch, at most SMs x resident CTAs per SM; about 610 KiB at most on
- *     a 152-SM GB300).  A call needing more gets MS_ERR_OUT_OF_MEMORY and
+ *   - The scratch must hold 4*m*G + 16 bytes (G = CTAs of the launch, at
+ *     most SMs x resident CTAs per SM; about 610 KiB at most on a 152-SM
+ *     GB300).  A call needing more gets MS_ERR_OUT_OF_MEMORY and
  *     nothing is enqueued.
  *   - Device-side failures (an expired bounded wait, a failed bounds check)
  *     are recorded in a word of the fixed array and are not reported by

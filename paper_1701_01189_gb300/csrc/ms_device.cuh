@@ -78,6 +78,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return wpre + x - v;
 }
 
+// Programmatic dependent launch: a kernel lets the next one in the stream
+// start early (launch_dependents); the dependent kernel waits for the earlier
+// grid to complete, and its writes to be visible, before reading its results.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Relaxed 64-bit loads and stores at GPU scope for look-back status words
 // (flag in the high half, value in the low half, so a reader never sees a
 // flag without its value).

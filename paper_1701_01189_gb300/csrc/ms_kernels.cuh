@@ -1,7 +1,7 @@
-// ms_kernels.cuh -- the local stages of the multisplit (Section 4.6 / 5.3):
-// pre-scan (per-chunk bucket histograms) and post-scan (stable local offsets,
-// block-level reordering in shared memory, coalesced scatter).  The global
-// stage between them is ms_scan.cuh.
+// ms_kernels.cuh -- the post-scan of the multisplit with warp-level ranks
+// (Section 4.6 / 5.3: stable local offsets, block-level reordering in shared
+// memory, coalesced scatter), used for m > 32 and as a tuning variant, and the
+// per-lane byte-counter flush of the pre-scan.  The pre-scan is ms_tc.cuh.
 //
 // Localization (Section 4.4; the "Block-level Multisplit" of Section 5.3):
 // each CTA owns a chunk of consecutive tiles (first level, one column of H per
@@ -11,16 +11,17 @@
 // (w, i, lane) sits at tile offset w*32*ITEMS + i*32 + lane, so that order is
 // the input order and the ranks below are stable.
 //
-// H is bucket-major, H[b * G + c], so one exclusive scan over the
-// row-vectorised H yields both global terms of Eq. 2.
+// H holds one count per (bucket b, chunk c), stored chunk-major as H[c * m +
+// b]; one exclusive scan over it in bucket-major (row-vectorised) order yields
+// both global terms of Eq. 2.
 //
 // GB300 budget: with ~22 bytes of HBM traffic per SM cycle to sustain, a
-// window of 32 keys may cost only ~11 ALU instructions in the pre-scan and ~22
-// in the post-scan.  Hence:
-//  * pre-scan: every lane keeps private 8-bit counters per bucket in shared
-//    memory (a load and a store per key, no voting); warps flush them into
-//    32-bit totals before any can overflow;
-//  * post-scan ranks: for m <= 4 the ballot voting of Section 5.4 (Alg. 2 and
+// window of 32 keys may cost only ~37 warp instructions in the post-scan.
+// Hence:
+//  * the pre-scan's per-lane 8-bit counters (ms_tc.cuh, m > 32): a
+//    fire-and-forget shared atomic per key in the lane's own bank, flushed by
+//    prescan_flush into 32-bit warp totals before any byte can overflow;
+//  * post-scan ranks: for m <= 32 the ballot voting of Section 5.4 (Alg. 2 and
 //    the corrected Alg. 3: one ballot per bucket bit); for larger m a per-warp
 //    "peer table" in shared memory: each lane ORs its lane bit into the entry
 //    of its bucket, reads back the mask of its peers, and the lowest peer
@@ -35,16 +36,6 @@
 
 namespace ms {
 
-struct PrescanArgs {
-  const uint32_t* keys;
-  uint32_t n;
-  DevSpec sp;
-  uint64_t chunk_elems;  // keys per chunk (the post-scan's tiles per chunk x its tile size)
-  uint32_t G;            // chunks (CTAs)
-  uint32_t* H;           // m * G, bucket-major
-  uint32_t prefetch;     // 1: bulk-prefetch the next tiles into L2
-};
-
 struct PostscanArgs {
   const uint32_t* keys_in;
   const uint32_t* vals_in;
@@ -55,7 +46,7 @@ struct PostscanArgs {
   uint32_t tiles_per_cta;
   uint32_t num_tiles;
   uint32_t G;
-  const uint32_t* Gx;  // exclusive scan of row-vectorised H (m*G entries)
+  const uint32_t* Gx;  // exclusive scan of row-vectorised H, stored chunk-major: Gx[c * m + b]
   uint32_t* err;       // device status word
   uint32_t prefetch;   // 1: bulk-prefetch the next tiles into L2
   uint32_t reverse;    // 1: walk the chunk's tiles last to first
@@ -99,67 +90,6 @@ __device__ __forceinline__ void prescan_flush(uint32_t* wwords, uint32_t* wtot, 
   __syncwarp();
   for (uint32_t q = 0; q < groups; ++q) wwords[q * 32 + lane] = 0u;
   __syncwarp();
-}
-
-// ---------------------------------------------------------------------------
-// Pre-scan.  Dynamic shared memory (words): splitter table (256), LUT, then
-// per warp m_pad * 8 words of byte counters, then per warp m_pad 32-bit totals.
-template <int KIND, int NB, int NW, int ITEMS, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB) k_prescan(PrescanArgs a) {
-  constexpr int T = NW * 32 * ITEMS;
-  extern __shared__ __align__(16) uint32_t smem[];
-  const DevSpec& sp = a.sp;
-  const uint32_t m_pad = sp.m_pad;
-  uint32_t* s_tbl = smem;
-  uint2* s_lut = reinterpret_cast<uint2*>(smem + 256);
-  uint32_t* s_words = smem + 256 + lut_words<KIND>(sp.lut_bits);  // NW * m_pad * 8 words
-  uint32_t* s_tot = s_words + NW * m_pad * 8;                      // NW * m_pad words
-
-  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
-  uint32_t* wwords = s_words + w * m_pad * 8;
-  uint32_t* wtot = s_tot + w * m_pad;
-  for (uint32_t i = threadIdx.x; i < NW * m_pad * 9; i += NW * 32) s_words[i] = 0u;  // counters + totals
-  build_bucket_tables<KIND, NB>(sp, s_tbl, s_lut);  // ends with a barrier
-
-  const uint32_t c = blockIdx.x;
-  const size_t begin = (size_t)c * a.chunk_elems;
-  const size_t end = min((size_t)a.n, begin + a.chunk_elems);
-  uint32_t since_flush = 0;  // keys counted per lane since the last flush
-  for (size_t tb = begin; tb < end; tb += T) {
-    if (a.prefetch && threadIdx.x == 0 && tb + 3 * (size_t)T <= end)
-      prefetch_l2(a.keys + tb + 2 * (size_t)T, T * 4u);  // a full tile only
-    const uint32_t* src = a.keys + tb;
-    const uint32_t rem = (uint32_t)min((size_t)T, end - tb);
-    const uint32_t off0 = w * (32 * ITEMS) + lane;
-    uint32_t key[ITEMS];
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) key[i] = (off0 + i * 32 < rem) ? src[off0 + i * 32] : 0u;
-    if (since_flush + ITEMS > 255u) {
-      prescan_flush(wwords, wtot, m_pad, lane);
-      since_flush = 0;
-    }
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      if (off0 + i * 32 < rem) {
-        const uint32_t b = bucket_of<KIND, NB>(key[i], sp, s_tbl, s_lut);
-        atomicAdd(wwords + ((b >> 2) << 5) + lane, 1u << ((b & 3u) << 3));
-      }
-    }
-    since_flush += ITEMS;
-  }
-  prescan_flush(wwords, wtot, m_pad, lane);
-  __syncthreads();
-  for (uint32_t b = threadIdx.x; b < sp.m; b += NW * 32) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int ww = 0; ww < NW; ++ww) s += s_tot[ww * m_pad + b];
-    a.H[(size_t)b * a.G + c] = s;
-  }
-}
-
-template <int KIND, int NW>
-__host__ size_t prescan_smem_bytes(uint32_t m_pad, uint32_t lut_bits) {
-  return 4u * (256u + lut_words<KIND>(lut_bits) + NW * m_pad * 9u);
 }
 
 // Ranks the ITEMS windows of one warp (Section 5.5: a direct solve per
@@ -322,7 +252,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
 
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   const uint32_t c = blockIdx.x;
-  const uint32_t len = m * a.G;
   const uint32_t t0 = c * a.tiles_per_cta;
   const uint32_t t1 = min(t0 + a.tiles_per_cta, a.num_tiles);
   const uint32_t ntiles = t1 > t0 ? t1 - t0 : 0u;
@@ -350,15 +279,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   }
   if (RANK == kRankTable)
     for (uint32_t i = threadIdx.x; i < 2 * NW * m_pad; i += THREADS) s_peer[i] = 0u;
-  // next global position of each bucket: chunk start (forward) or chunk end (reverse)
-  for (uint32_t b = threadIdx.x; b < m; b += THREADS) {
-    const uint32_t e = b * a.G + c;
-    s_run[b] = a.reverse ? ((e + 1 < len) ? a.Gx[e + 1] : a.n) : a.Gx[e];
-  }
   __syncthreads();  // mbarriers initialised
   if (threadIdx.x == 0)
-    for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);
+    for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);  // inputs are not written by the pre-scan
   build_bucket_tables<KIND, NB>(sp, s_tbl, s_lut);  // ends with a barrier
+  pdl_wait();  // H scanned by the pre-scan grid
+  // next global position of each bucket: chunk start (forward) or chunk end (reverse)
+  for (uint32_t b = threadIdx.x; b < m; b += THREADS) {  // Gx chunk-major: Gx[c * m + b]
+    const uint32_t next = (c + 1 < a.G) ? a.Gx[(size_t)(c + 1) * m + b] : (b + 1 < m ? a.Gx[b + 1] : a.n);
+    s_run[b] = a.reverse ? next : a.Gx[(size_t)c * m + b];
+  }
+  __syncthreads();
 
   uint32_t* wc = s_cnt + w * S;
   uint32_t* wpeer = s_peer + w * 2 * m_pad;

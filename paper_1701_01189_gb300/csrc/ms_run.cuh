@@ -61,40 +61,29 @@ static inline Chunking make_chunking(uint32_t n, uint32_t T, uint32_t max_ctas) 
 
 namespace ms {
 
-// Pre-scan tile: 8 warps x 16 keys per lane.  Its NB only sizes the splitter
-// search of range buckets; 8 covers every m.
-constexpr int kPreNW = 8, kPreItems = 16, kPreMinB = 3;
-
 template <int KIND, int NB, int NW, int ITEMS, bool PAIRS, int RANK, int REORDER, int MINB, int STAGES = 2>
 static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   constexpr int THREADS = NW * 32;
   constexpr uint32_t T = THREADS * ITEMS;
-  constexpr int NBPRE = KIND == kRange ? 8 : 0;
-  auto kpre = k_prescan<KIND, NBPRE, kPreNW, kPreItems, kPreMinB>;
+  static_assert(kTcTile % T == 0, "post-scan tiles divide the pre-scan's");
   auto kpost = k_postscan<KIND, NB, NW, ITEMS, PAIRS, RANK, REORDER, MINB, STAGES>;
   const uint32_t m_pad = c.sp.m_pad, lb = c.sp.lut_bits;
   const uint32_t mp_max = RANK == kRankBallot ? 32u : 256u;
-  const size_t smem_pre_max = prescan_smem_bytes<KIND, kPreNW>(256, 11);
   const size_t smem_post_max = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>(mp_max, 11);
-  const size_t smem_pre = prescan_smem_bytes<KIND, kPreNW>(m_pad, lb);
   const size_t smem_post = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>(m_pad, lb);
-  static LaunchInfo li_pre, li_post;
+  static LaunchInfo li_post;
   const int nb_post = setup_kernel(li_post, kpost, THREADS, smem_post_max, smem_post, ctx.device);
-  const int nb_pre = setup_kernel(li_pre, kpre, kPreNW * 32, smem_pre_max, smem_pre, ctx.device);
 
-  // One chunk per CTA in both kernels; the pre-scan CTAs walk the same chunks
-  // of K*T keys with their own tile size.
-  const int resident = std::min(nb_post, nb_pre);
-  const Chunking ch = make_chunking(c.n, T, (uint32_t)(ctx.sm_count * resident));
+  // One chunk per CTA in both kernels: whole 4096-key pre-scan tiles, walked
+  // by the post-scan in its own tiles.
+  const Chunking ch = make_chunking(c.n, kTcTile, (uint32_t)(ctx.sm_count * nb_post));
+  const uint32_t post_k = ch.K * (kTcTile / T);
+  const uint32_t post_l = (uint32_t)(((uint64_t)c.n + T - 1) / T);
   const uint32_t m = c.sp.m;
-  const uint32_t len = m * ch.G;
-  const uint32_t nscan = (len + kScanTile - 1) / kScanTile;
 
-  // scratch: H (len words, 16-byte aligned) | scan status (nscan u64) | ticket
-  // | (histogram only) offsets
-  const size_t h_bytes = ((size_t)len * 4 + 15) & ~(size_t)15;
-  const size_t st_bytes = (size_t)nscan * 8;
-  const size_t bytes = h_bytes + st_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
+  // scratch: H (m * G words, 16-byte aligned) | arrival counter | (histogram only) offsets
+  const size_t h_bytes = ((size_t)m * ch.G * 4 + 15) & ~(size_t)15;
+  const size_t bytes = h_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
   void* ws = nullptr;
   cudaError_t e = cudaSuccess;
   if (c.ws_fixed != nullptr) {
@@ -105,34 +94,27 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
     if (e != cudaSuccess) return e;
   }
   uint32_t* H = static_cast<uint32_t*>(ws);
-  auto* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + h_bytes);
-  auto* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes);
-  e = cudaMemsetAsync(status, 0, st_bytes + 16, c.stream);
+  uint32_t* arrive = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes);
+  e = cudaMemsetAsync(arrive, 0, 16, c.stream);
 
   const uint32_t aligned =
       ((reinterpret_cast<uintptr_t>(c.keys_in) | reinterpret_cast<uintptr_t>(c.vals_in)) & 15u) == 0;
   const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
-  if (e == cudaSuccess) {
-    PrescanArgs pa{c.keys_in, c.n, c.sp, (uint64_t)ch.K * T, ch.G, H, aligned};
-    kpre<<<ch.G, kPreNW * 32, smem_pre, c.stream>>>(pa);
-    e = cudaGetLastError();
-    trace_mark(slot, 1, c.stream);
-  }
   uint32_t* offsets = c.offsets;
-  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes + 16);
+  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + 16);
   if (e == cudaSuccess) {
-    ScanArgs sa{H, len, ch.G, offsets, m, status, ticket, ctx.d_err};
-    e = launch_scan_lookback(sa, c.stream);
-    trace_mark(slot, 2, c.stream);
+    e = launch_prescan<KIND>(c, ctx, ch, H, arrive, offsets);
+    trace_mark(slot, 1, c.stream);
+    trace_mark(slot, 2, c.stream);  // the global scan runs inside the pre-scan
   }
   if (e == cudaSuccess && c.counts != nullptr) {
     e = launch_counts_from_offsets(offsets, c.counts, m, c.stream);
     trace_mark(slot, 3, c.stream);
   } else if (e == cudaSuccess) {
-    PostscanArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, c.sp, ch.K, ch.L, ch.G, H, ctx.d_err,
+    PostscanArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, c.sp, post_k, post_l, ch.G, H, ctx.d_err,
                     aligned, 1u};
-    kpost<<<ch.G, THREADS, smem_post, c.stream>>>(qa);
-    e = cudaGetLastError();
+    // stage timing records events between the kernels: then a plain launch
+    e = launch_dependent(kpost, ch.G, THREADS, smem_post, c.stream, slot >= 0, qa);
     trace_mark(slot, 3, c.stream);
   }
   const cudaError_t e2 = c.ws_fixed != nullptr ? cudaSuccess : scratch_free(ws, c.stream);

@@ -48,29 +48,76 @@ inline bool make_tile_map(CUtensorMap* map, const uint32_t* base, uint32_t n, ui
   return r == CUDA_SUCCESS;
 }
 
+// Launches `kernel` on `s` as a programmatic dependent of the kernel before it
+// (it may start while that one drains; it waits with griddepcontrol.wait
+// before reading that kernel's results), unless `plain`.
+template <typename K, typename... Args>
+static cudaError_t launch_dependent(K kernel, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t s,
+                                    bool plain, Args... args) {
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = plain ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Bytes of L2 the pre-scan asks to keep (evict_last) for the post-scan: the
 // last tiles of every chunk, about half of the 126 MB L2.
 constexpr size_t kTcL2KeepBytes = (size_t)64 << 20;
 
+// The pre-scan of every design: `k_prescan_tc` (ms_tc.cuh) counting in
+// registers (m <= 8), per-thread counters (m <= 32) or per-lane byte counters
+// (m <= 256), its last CTA scanning H.  Chunks are whole 4096-key tiles.
+template <int KIND>
+static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking& ch, uint32_t* H, uint32_t* arrive,
+                                  uint32_t* offsets) {
+  const uint32_t m = c.sp.m;
+  const int mode = m <= 8 ? kCountReg : m <= 32 ? kCountThread : kCountLaneBytes;
+  // splitter lookup tables: 1024 cells x 8 copies (m <= 32), 2048 cells x 2 copies beyond
+  const uint32_t lb = mode == kCountLaneBytes ? 11u : 10u, lw = mode == kCountLaneBytes ? 1u : 3u;
+  const bool vec = ((reinterpret_cast<uintptr_t>(c.keys_in)) & 15u) == 0;
+  const size_t keep_tiles = kTcL2KeepBytes / ((size_t)kTcTile * 4);
+  const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
+  TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, arrive, offsets, lb, lw, c.sp};
+  static LaunchInfo li[3];
+  if (mode == kCountLaneBytes) {
+    auto k = k_prescan_tc<KIND, kCountLaneBytes>;
+    const size_t smem = tc_prescan_smem<KIND, kCountLaneBytes>(m, lb, lw);
+    setup_kernel(li[2], k, kTcThreads, tc_prescan_smem<KIND, kCountLaneBytes>(kMaxM, lb, lw), smem, ctx.device);
+    k<<<ch.G, kTcThreads, smem, c.stream>>>(pa);
+  } else if (mode == kCountThread) {
+    auto k = k_prescan_tc<KIND, kCountThread>;
+    const size_t smem = tc_prescan_smem<KIND, kCountThread>(m, lb, lw);
+    setup_kernel(li[0], k, kTcThreads, tc_prescan_smem<KIND, kCountThread>(kTcMaxM, lb, lw), smem, ctx.device);
+    k<<<ch.G, kTcThreads, smem, c.stream>>>(pa);
+  } else {
+    auto k = k_prescan_tc<KIND, kCountReg>;
+    const size_t smem = tc_prescan_smem<KIND, kCountReg>(m, lb, lw);
+    setup_kernel(li[1], k, kTcThreads, tc_prescan_smem<KIND, kCountReg>(kTcMaxM, lb, lw), smem, ctx.device);
+    k<<<ch.G, kTcThreads, smem, c.stream>>>(pa);
+  }
+  return cudaGetLastError();
+}
+
 template <int KIND, bool PAIRS, int STAGES, int KPT>
 static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   constexpr uint32_t T = kTcThreads * KPT;  // post-scan tile; the pre-scan works in 4096-key tiles
-  const bool small_m = c.sp.m <= 8;
-  auto kpre = small_m ? k_prescan_tc<KIND, true> : k_prescan_tc<KIND, false>;
   auto kpost = k_postscan_tc<KIND, PAIRS, STAGES, KPT>;
   using Lay = TcPostLayout<KIND, PAIRS, STAGES, KPT>;
   const DevSpec& sp = c.sp;
-  // splitter lookup tables: 1024 cells x 8 copies for the pre-scan; 512 cells
-  // x 4 copies for the post-scan (x 2 for key-value pairs with more than 16
-  // buckets, which keeps two CTAs of the post-scan per SM)
-  const uint32_t pre_lb = 10, pre_lw = 3;
+  // splitter lookup table of the post-scan: 512 cells x 4 copies (x 2 for
+  // key-value pairs with more than 16 buckets, which keeps two CTAs per SM)
   const uint32_t post_lb = 9, post_lw = (PAIRS && sp.m > 16) ? 1u : 2u;
-  const size_t smem_pre = tc_prescan_smem<KIND>(sp.m, pre_lb, pre_lw);
   const size_t smem_post = Lay::bytes(sp.m, post_lb, post_lw);
-  static LaunchInfo li_pre_s, li_pre_l, li_post;
+  static LaunchInfo li_post;
   const int nb_post = setup_kernel(li_post, kpost, kTcThreads, Lay::bytes(kTcMaxM, post_lb, 2), smem_post, ctx.device);
-  setup_kernel(small_m ? li_pre_s : li_pre_l, kpre, kTcThreads, tc_prescan_smem<KIND>(kTcMaxM, pre_lb, pre_lw),
-               smem_pre, ctx.device);
 
   // chunks are whole 4096-key pre-scan tiles; the post-scan walks them in its own tiles
   const Chunking ch = make_chunking(c.n, kTcTile, (uint32_t)(ctx.sm_count * nb_post));
@@ -93,23 +140,17 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   uint32_t* arrive = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes);
   e = cudaMemsetAsync(arrive, 0, 16, c.stream);
 
-  const bool vec = ((reinterpret_cast<uintptr_t>(c.keys_in)) & 15u) == 0;
   CUtensorMap tmk, tmv;
   std::memset(&tmk, 0, sizeof tmk);
   std::memset(&tmv, 0, sizeof tmv);
   bool tma = make_tile_map(&tmk, c.keys_in, c.n, T);
   if (tma && PAIRS) tma = make_tile_map(&tmv, c.vals_in, c.n, T);
 
-  // the last `keep` tiles of every chunk are read with evict_last
-  const size_t keep_tiles = kTcL2KeepBytes / ((size_t)kTcTile * 4);
-  const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
   const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
   uint32_t* offsets = c.offsets;
   if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + 16);
   if (e == cudaSuccess) {
-    TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, arrive, offsets, pre_lb, pre_lw, sp};
-    kpre<<<ch.G, kTcThreads, smem_pre, c.stream>>>(pa);
-    e = cudaGetLastError();
+    e = launch_prescan<KIND>(c, ctx, ch, H, arrive, offsets);
     trace_mark(slot, 1, c.stream);
     trace_mark(slot, 2, c.stream);  // the global scan runs inside the pre-scan
   }
@@ -119,18 +160,8 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   } else if (e == cudaSuccess) {
     TcPostArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, post_k, post_l, ch.G, H, ctx.d_err,
                   tma ? 1u : 0u, post_lb, post_lw, sp};
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof cfg);
-    cfg.gridDim = dim3(ch.G);
-    cfg.blockDim = dim3(kTcThreads);
-    cfg.dynamicSmemBytes = smem_post;
-    cfg.stream = c.stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = slot < 0 ? 1 : 0;  // stage timing records events between the kernels
-    e = cudaLaunchKernelEx(&cfg, kpost, tmk, tmv, qa);
+    // stage timing records events between the kernels: then a plain launch
+    e = launch_dependent(kpost, ch.G, kTcThreads, smem_post, c.stream, slot >= 0, tmk, tmv, qa);
     trace_mark(slot, 3, c.stream);
   }
   const cudaError_t e2 = c.ws_fixed != nullptr ? cudaSuccess : scratch_free(ws, c.stream);

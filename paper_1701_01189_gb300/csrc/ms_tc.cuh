@@ -37,6 +37,7 @@
 #include <cuda.h>
 
 #include "ms_bucket.cuh"
+#include "ms_kernels.cuh"
 #include "ms_tma.cuh"
 
 namespace ms {
@@ -65,8 +66,6 @@ __device__ __forceinline__ uint32_t tc_swz(uint32_t p) { return p ^ (((p >> 5) &
 // and the write-out of 32 consecutive positions both hit 32 different banks.
 __device__ __forceinline__ uint32_t tc_rswz(uint32_t p) { return p ^ ((p >> 5) & 31u); }
 
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // 16-byte read-only load that does not allocate in L1, with an L2 policy.
 __device__ __forceinline__ uint4 ldg_v4_policy(const uint32_t* p, uint64_t policy) {
@@ -112,41 +111,43 @@ __device__ __forceinline__ uint32_t tc_block_scan(uint32_t v, uint32_t* s_warp, 
   return pre + x - v;
 }
 
-// Splitter lookup table of these kernels (range buckets, m <= 32): 2^lb
-// cells of the key space (its top lb bits), each one 32-bit word -- the
-// bucket of the cell's first key (bits 0..4), a flag for a cell holding two
-// or more splitters (bit 5), and the low 32 - lb bits of the cell's single
-// splitter (bits 6..31; 2^(32-lb), above every key, when it holds none) --
-// stored W = 2^lw times side by side: lane l reads copy l mod W, so a warp's
-// random lookups spread over W times as many banks.  A flagged cell's keys
-// take the full search over the splitter table (tc_fixup).  lb >= 7.
-constexpr uint32_t kTcLutFlag = 32u;
+// Splitter lookup table of these kernels (range buckets): 2^lb cells of the
+// key space (its top lb bits), each one 32-bit word -- the bucket of the
+// cell's first key (bits 0..BB-1; BB = 5 for m <= 32, 8 for m <= 256), a flag
+// for a cell holding two or more splitters (bit BB), and the low 32 - lb bits
+// of the cell's single splitter (from bit BB+1; 2^(32-lb), above every key,
+// when it holds none) -- stored W = 2^lw times side by side: lane l reads copy
+// l mod W, so a warp's random lookups spread over W times as many banks.  A
+// flagged cell's keys take the full search over the splitter table
+// (tc_fixup).  Needs 32 - lb <= 30 - BB.
+constexpr uint32_t kTcLutFlag = 32u;  // the flag bit for BB = 5
 
 __host__ __device__ constexpr uint32_t tc_lut_words(int kind, uint32_t lb, uint32_t lw) {
   return kind == kRange ? (1u << (lb + lw)) : 0u;
 }
 
-// Splitter table (31 entries, padded with 0xffffffff) and lookup table.  All
-// threads of the block call it; ends with a block barrier.
-template <int KIND>
+// Splitter table (2^BB - 1 entries, padded with 0xffffffff) and lookup table.
+// All threads of the block call it; ends with a block barrier.
+template <int KIND, int BB = 5>
 __device__ __forceinline__ void tc_build_tables(const DevSpec& sp, uint32_t lb, uint32_t lw, uint32_t* tbl,
                                                 uint32_t* lut) {
   if constexpr (KIND == kRange) {
-    for (uint32_t i = threadIdx.x; i < 31u; i += blockDim.x) tbl[i] = (i + 1 < sp.m) ? sp.splitters[i] : 0xffffffffu;
+    constexpr uint32_t P = (1u << BB) - 1u;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) tbl[i] = (i + 1 < sp.m) ? sp.splitters[i] : 0xffffffffu;
     __syncthreads();
     const uint32_t sh = 32u - lb, fmask = (1u << sh) - 1u, W = 1u << lw, m = sp.m;
     for (uint32_t cell = threadIdx.x; cell < (1u << lb); cell += blockDim.x) {
       const uint32_t first = cell << sh, last = first | fmask;
       // splitters <= x, clamped to m - 1, is the bucket of x
-      const uint32_t lo = min(first == 0u ? 0u : range_search<5>(first - 1u, tbl, m + 1u), m - 1u);
-      const uint32_t hi = min(range_search<5>(last, tbl, m + 1u), m - 1u);
+      const uint32_t lo = min(first == 0u ? 0u : range_search<BB>(first - 1u, tbl, m + 1u), m - 1u);
+      const uint32_t hi = min(range_search<BB>(last, tbl, m + 1u), m - 1u);
       uint32_t e;
       if (hi == lo)
-        e = lo | ((fmask + 1u) << 6);
+        e = lo | ((fmask + 1u) << (BB + 1));
       else if (hi == lo + 1u)
-        e = lo | ((tbl[lo] & fmask) << 6);
+        e = lo | ((tbl[lo] & fmask) << (BB + 1));
       else
-        e = kTcLutFlag;
+        e = 1u << BB;
       for (uint32_t r = 0; r < W; ++r) lut[(cell << lw) + r] = e;
     }
   }
@@ -165,30 +166,31 @@ struct TcLut {
   __device__ __forceinline__ uint32_t word(uint32_t u) const { return lut[((u >> sh) << lw) + rep]; }
 };
 
-template <int KIND>
+template <int KIND, int BB = 5>
 __device__ __forceinline__ uint32_t tc_bucket(uint32_t u, const DevSpec& sp, const TcLut& L, uint32_t& flag) {
   if constexpr (KIND == kRange) {
     const uint32_t e = L.word(u);
     flag |= e;
-    return (e & 31u) + ((u & L.fmask) >= (e >> 6) ? 1u : 0u);
+    return (e & ((1u << BB) - 1u)) + ((u & L.fmask) >= (e >> (BB + 1)) ? 1u : 0u);
   } else {
-    return bucket_of<KIND, 5>(u, sp, nullptr, nullptr);
+    return bucket_of<KIND, BB>(u, sp, nullptr, nullptr);
   }
 }
 
-template <int N>
+template <int N, int BB = 5>
 __device__ __forceinline__ void tc_fixup(const uint32_t (&key)[N], uint32_t (&bk)[N], const TcLut& L,
                                          const uint32_t* tbl, uint32_t m) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    if (L.word(key[i]) & kTcLutFlag) bk[i] = range_search<5>(key[i], tbl, m);
+    if (L.word(key[i]) & (1u << BB)) bk[i] = range_search<BB>(key[i], tbl, m);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Pre-scan: per-chunk bucket histograms (column c of H, bucket-major
-// H[b * G + c]), then, in the last CTA to finish, the exclusive scan of the
-// row-vectorised H in place and the bucket offsets.
+// Pre-scan: per-chunk bucket histograms (column c of H, stored chunk-major as
+// H[c * m + b] so that a column is one coalesced write), then, in the last CTA
+// to finish, the exclusive scan of the row-vectorised (bucket-major) H in
+// place and the bucket offsets.
 struct TcPreArgs {
   const uint32_t* keys;
   uint32_t n;
@@ -197,39 +199,51 @@ struct TcPreArgs {
   uint32_t G;                // chunks (CTAs)
   uint32_t keep_from;        // chunk-relative tile index from which loads keep their lines in L2
   uint32_t vec;              // keys 16-byte aligned
-  uint32_t* H;               // m * G words; becomes the exclusive scan
+  uint32_t* H;               // m * G words, chunk-major H[c * m + b]; becomes the exclusive scan
   uint32_t* arrive;          // zero before the launch
   uint32_t* offsets;         // m + 1 words, or nullptr
   uint32_t lb, lw;           // lookup table: 2^lb cells, 2^lw copies (range buckets)
   DevSpec sp;
 };
 
-template <int KIND>
+// How the pre-scan counts: per-(bucket, thread) 32-bit counters (m <= 32),
+// eight 8-bit counters in one 64-bit register per thread (m <= 8), or
+// per-lane 8-bit counters per warp, four buckets to a word in the lane's own
+// bank (m <= 256).
+enum TcCount : int { kCountThread = 0, kCountReg = 1, kCountLaneBytes = 2 };
+
+__host__ __device__ constexpr uint32_t tc_mpad(uint32_t m) { return m <= 32 ? 32u : ((m + 31u) & ~31u); }
+
+template <int KIND, int MODE>
 __host__ size_t tc_prescan_smem(uint32_t m, uint32_t lb, uint32_t lw) {
-  return 4u * (size_t)(tc_rows(m) * kTcRow + 32u + tc_lut_words(KIND, lb, lw));
+  const uint32_t cnt_words = MODE == kCountLaneBytes ? (kTcThreads / 32) * tc_mpad(m) * 9u : tc_rows(m) * kTcRow;
+  const uint32_t tbl_words = MODE == kCountLaneBytes ? 256u : 32u;
+  return 4u * (size_t)(cnt_words + tbl_words + tc_lut_words(KIND, lb, lw));
 }
 
-// SMALLM (m <= 8): each thread counts its keys in one 64-bit register of
-// eight 8-bit fields (no shared-memory traffic per key), flushed into its
-// shared counters before a field can overflow.
-template <int KIND, bool SMALLM>
-__global__ void __launch_bounds__(kTcThreads, 3) k_prescan_tc(TcPreArgs a) {
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k_prescan_tc(TcPreArgs a) {
+  constexpr int BB = MODE == kCountLaneBytes ? 8 : 5;  // bits of a bucket in the lookup table
+  constexpr int NW = kTcThreads / 32;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_warp[8];
   __shared__ uint32_t s_last;
   const DevSpec& sp = a.sp;
-  const uint32_t m = sp.m, R = tc_rows(m);
+  const uint32_t m = sp.m, R = tc_rows(m), m_pad = tc_mpad(m);
+  const uint32_t cnt_words = MODE == kCountLaneBytes ? NW * m_pad * 9u : R * kTcRow;
   uint32_t* s_cnt = smem;
-  uint32_t* s_tbl = smem + R * kTcRow;
-  uint32_t* s_lut = s_tbl + 32;
+  uint32_t* s_tbl = smem + cnt_words;
+  uint32_t* s_lut = s_tbl + (MODE == kCountLaneBytes ? 256u : 32u);
   const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
   const TcLut L{s_lut, 32u - a.lb, a.lw, lane & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u};
 
-  for (uint32_t i = t; i < R * kTcRow; i += kTcThreads) s_cnt[i] = 0u;
-  tc_build_tables<KIND>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
+  for (uint32_t i = t; i < cnt_words; i += kTcThreads) s_cnt[i] = 0u;
+  tc_build_tables<KIND, BB>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
   pdl_launch_dependents();
 
-  uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)
+  uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // kCountThread/kCountReg: counter (bucket 0, thread t)
+  uint32_t* wwords = s_cnt + w * m_pad * 8u;   // kCountLaneBytes: this warp's byte counters
+  uint32_t* wtot = s_cnt + NW * m_pad * 8u + w * m_pad;  // ... and its 32-bit totals
   const uint32_t c = blockIdx.x;
   const uint32_t t0 = c * a.tiles_per_chunk;
   const uint32_t t1 = min(t0 + a.tiles_per_chunk, a.num_tiles);
@@ -237,32 +251,41 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_prescan_tc(TcPreArgs a) {
   const uint32_t tv1 = a.vec ? max(t0, min(t1, nfull)) : t0;
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
 
-  uint64_t creg = 0;     // SMALLM: eight 8-bit counters
-  uint32_t creg_keys = 0;  // keys in creg since its last flush
+  uint64_t creg = 0;       // kCountReg: eight 8-bit counters
+  uint32_t since = 0;      // keys counted by this thread since the last flush
   auto flush = [&]() {
-    for (uint32_t b = 0; b < m; ++b) {
-      const uint32_t v = (uint32_t)(creg >> (8u * b)) & 0xffu;
-      if (v) atomicAdd(my + b * kTcRow, v);
+    if constexpr (MODE == kCountReg) {
+      for (uint32_t b = 0; b < m; ++b) {
+        const uint32_t v = (uint32_t)(creg >> (8u * b)) & 0xffu;
+        if (v) atomicAdd(my + b * kTcRow, v);
+      }
+      creg = 0;
+    } else if constexpr (MODE == kCountLaneBytes) {
+      prescan_flush(wwords, wtot, m_pad, lane);
     }
-    creg = 0;
-    creg_keys = 0;
+    since = 0;
+  };
+  auto count1 = [&](uint32_t b) {
+    if constexpr (MODE == kCountThread) {
+      atomicAdd(my + b * kTcRow, 1u);
+    } else if constexpr (MODE == kCountReg) {
+      creg += 1ull << (8u * b);
+    } else {
+      atomicAdd(wwords + ((b >> 2) << 5) + lane, 1u << ((b & 3u) << 3));
+    }
   };
   auto count16 = [&](uint32_t (&key)[16]) {
     uint32_t bk[16];
     uint32_t flag = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND, BB>(key[i], sp, L, flag);
     if constexpr (KIND == kRange)
-      if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
-    if constexpr (SMALLM) {
-      if (creg_keys + 16u > 255u) flush();
+      if (flag & (1u << BB)) tc_fixup<16, BB>(key, bk, L, s_tbl, m);
+    if constexpr (MODE != kCountThread)
+      if (since + 16u > 255u) flush();  // a byte counter must not overflow
 #pragma unroll
-      for (int i = 0; i < 16; ++i) creg += 1ull << (8u * bk[i]);
-      creg_keys += 16u;
-    } else {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) atomicAdd(my + bk[i] * kTcRow, 1u);
-    }
+    for (int i = 0; i < 16; ++i) count1(bk[i]);
+    since += 16u;
   };
   // thread (w, lane) holds words w*512 + j*128 + 4*lane + e of the tile
   auto load16 = [&](uint32_t (&key)[16], uint32_t tile) {
@@ -291,31 +314,45 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_prescan_tc(TcPreArgs a) {
       count16(kb);
     }
   }
-  // the partial last tile, or every tile of an unaligned input
+  // the partial last tile, or every tile of an unaligned input (at most 16
+  // keys per thread per tile, so the byte counters are flushed per tile)
   for (uint32_t tile = tv1; tile < t1; ++tile) {
     const size_t tb = (size_t)tile * kTcTile;
     const uint32_t rem = (uint32_t)min((size_t)kTcTile, (size_t)a.n - tb);
+    if constexpr (MODE != kCountThread)
+      if (since + 16u > 255u) flush();
     for (uint32_t p = t; p < rem; p += kTcThreads) {
       uint32_t flag = 0;
       const uint32_t u = a.keys[tb + p];
-      uint32_t b = tc_bucket<KIND>(u, sp, L, flag);
+      uint32_t b = tc_bucket<KIND, BB>(u, sp, L, flag);
       if constexpr (KIND == kRange)
-        if (flag & kTcLutFlag) b = range_search<5>(u, s_tbl, m);
-      atomicAdd(my + b * kTcRow, 1u);
+        if (flag & (1u << BB)) b = range_search<BB>(u, s_tbl, m);
+      count1(b);
     }
+    since += 16u;
   }
-  if constexpr (SMALLM) flush();
+  if constexpr (MODE != kCountThread) flush();
   __syncthreads();
 
-  // column c of H: warp w sums buckets w, w+8, w+16, w+24 over the 256 threads
-  for (uint32_t b = w; b < m; b += kTcThreads / 32) {
-    const uint32_t* row = s_cnt + b * kTcRow + lane;
-    uint32_t s = 0;
+  if constexpr (MODE == kCountLaneBytes) {
+    // column c of H: the warps' totals summed per bucket
+    for (uint32_t b = t; b < m; b += kTcThreads) {
+      uint32_t s2 = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s += row[36 * k];
+      for (int ww = 0; ww < NW; ++ww) s2 += s_cnt[NW * m_pad * 8u + ww * m_pad + b];
+      a.H[(size_t)c * m + b] = s2;
+    }
+  } else {
+    // column c of H: warp w sums buckets w, w+8, w+16, w+24 over the 256 threads
+    for (uint32_t b = w; b < m; b += kTcThreads / 32) {
+      const uint32_t* row = s_cnt + b * kTcRow + lane;
+      uint32_t s2 = 0;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
-    if (lane == 0) a.H[(size_t)b * a.G + c] = s;
+      for (int k = 0; k < 8; ++k) s2 += row[36 * k];
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) s2 += __shfl_xor_sync(kFull, s2, d);
+      if (lane == 0) a.H[(size_t)c * m + b] = s2;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -324,33 +361,31 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_prescan_tc(TcPreArgs a) {
   if (s_last == 0u) return;
   __threadfence();
 
-  // last CTA: exclusive scan of H_row in place (Eq. 2), bucket offsets
-  const uint32_t len = m * a.G;
-  uint32_t carry = 0;
-  for (uint32_t base = 0; base < len; base += kTcTile) {
-    uint32_t v[16];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const uint32_t idx = base + 16u * t + i;
-      v[i] = idx < len ? __ldcg(a.H + idx) : 0u;
-      sum += v[i];
-    }
-    uint32_t total;
-    uint32_t run = carry + tc_block_scan(sum, s_warp, &total);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const uint32_t idx = base + 16u * t + i;
-      if (idx < len) {
-        a.H[idx] = run;
-        if (a.offsets != nullptr && idx % a.G == 0u) a.offsets[idx / a.G] = run;
-      }
-      run += v[i];
-    }
-    carry += total;
-    __syncthreads();  // s_warp is rewritten by the next round
+  // Last CTA: exclusive scan of H_row in place (Eq. 2) -- in bucket-major
+  // order, with H stored chunk-major -- and the bucket offsets.  Thread b
+  // owns bucket b: it sums its row (the G chunk counts, coalesced across the
+  // threads), one block scan of the row sums gives the buckets' bases, then it
+  // writes the running prefix of its row.  Two passes of G independent loads
+  // per thread instead of a serial walk over the matrix.
+  uint32_t row = 0;
+  if (t < m) {
+#pragma unroll 8
+    for (uint32_t cc = 0; cc < a.G; ++cc) row += __ldcg(a.H + (size_t)cc * m + t);
   }
-  if (t == 0 && a.offsets != nullptr) a.offsets[m] = carry;
+  uint32_t total;
+  const uint32_t base = tc_block_scan(row, s_warp, &total);  // m <= 256 = threads
+  if (t < m) {
+    uint32_t run = base;
+#pragma unroll 8
+    for (uint32_t cc = 0; cc < a.G; ++cc) {
+      uint32_t* h = a.H + (size_t)cc * m + t;
+      const uint32_t v = __ldcg(h);
+      *h = run;
+      run += v;
+    }
+    if (a.offsets != nullptr) a.offsets[t] = base;
+  }
+  if (t == 0 && a.offsets != nullptr) a.offsets[m] = total;
 }
 
 // ---------------------------------------------------------------------------
@@ -364,7 +399,7 @@ struct TcPostArgs {
   uint32_t tiles_per_cta;
   uint32_t num_tiles;
   uint32_t G;
-  const uint32_t* Gx;  // exclusive scan of row-vectorised H (m * G entries)
+  const uint32_t* Gx;  // exclusive scan of row-vectorised H, stored chunk-major: Gx[c * m + b]
   uint32_t* err;       // device status word
   uint32_t tma;        // 1: full tiles arrive by tensor copies (inputs 16-byte aligned)
   uint32_t lb, lw;     // lookup table: 2^lb cells, 2^lw copies (range buckets)
@@ -446,11 +481,8 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
     for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);  // inputs are not written by the pre-scan
   tc_build_tables<KIND>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
   pdl_wait();  // H scanned by the pre-scan grid
-  const uint32_t len = m * a.G;
-  for (uint32_t b = t; b < m; b += kTcThreads) {
-    const uint32_t e = b * a.G + c;
-    s_run[b] = (e + 1u < len) ? a.Gx[e + 1u] : a.n;  // end of bucket b's share of this chunk
-  }
+  for (uint32_t b = t; b < m; b += kTcThreads)  // end of bucket b's share of this chunk (Gx chunk-major)
+    s_run[b] = (c + 1u < a.G) ? a.Gx[(size_t)(c + 1u) * m + b] : (b + 1u < m ? a.Gx[b + 1u] : a.n);
   __syncthreads();
 
   uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)

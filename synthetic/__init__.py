@@ -16,6 +16,11 @@ distributions) and the sizes of the benchmark configurations:
 * float32 keys uniform in [0, 1000): u = uint32 draw, x = float32(u >> 8) *
   2^-24 (exact), then x * 1000.0f rounded to float32 (the largest value is
   999.99993896484375 < 1000);
+* Section 6.4's non-uniform workloads for delta buckets of width delta over
+  [0, m*delta): a bucket slot b drawn from the binomial B(m-1, p) or from the
+  "alpha-uniform" mix (a fraction alpha uniform over the m slots, the rest in
+  one random slot), then a float32 key in the middle half of the slot,
+  x = float32((b + u) * delta) with u uniform in [0.25, 0.75);
 * values = original index (makes stability visible) or uniform uint32;
 * batched segments: size = floor(2^U), U ~ Uniform(lo, hi);
 * serving traces: Poisson arrivals (exponential gaps) with a request mix.
@@ -82,6 +87,28 @@ def uniform_f32_1000(n: int, seed: int) -> np.ndarray:
     x = (u >> np.uint32(8)).astype(np.float32) * np.float32(2.0 ** -24)
     x = x * np.float32(1000.0)
     return x.astype(np.float32).view(np.uint32)
+
+
+def _f32_in_slots(b: np.ndarray, delta: float, g: np.random.Generator) -> np.ndarray:
+    u = g.uniform(0.25, 0.75, size=b.shape[0])
+    x = ((b.astype(np.float64) + u) * float(np.float32(delta))).astype(np.float32)
+    return x.view(np.uint32)
+
+
+def binomial_f32(n: int, m: int, delta: float, seed: int, p: float = 0.5) -> np.ndarray:
+    """float32 keys (as uint32 bit patterns) whose delta-bucket slot is B(m-1, p)."""
+    g = rng(seed)
+    b = g.binomial(m - 1, p, size=int(n))
+    return _f32_in_slots(b, delta, g)
+
+
+def alpha_uniform_f32(n: int, m: int, delta: float, alpha: float, seed: int) -> np.ndarray:
+    """float32 keys: a fraction alpha with a uniform slot in [0, m), the rest
+    all in one random slot (Section 6.4's "alpha-uniform" distribution)."""
+    g = rng(seed)
+    hot = int(g.integers(0, m))
+    b = np.where(g.random(size=int(n)) < alpha, g.integers(0, m, size=int(n)), hot)
+    return _f32_in_slots(b, delta, g)
 
 
 def segment_sizes(num: int, lo_log2: float, hi_log2: float, seed: int) -> np.ndarray:

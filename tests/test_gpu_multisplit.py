@@ -171,3 +171,17 @@ def test_config_sweep_2p26_f32(m):
     case = Case(oracle.DELTA_F32, m, x0=0.0, delta=float(np.float32(1000.0) / np.float32(m)))
     check_multisplit(keys, None, case)
     check_multisplit(keys, synthetic.index_values(n), case)
+
+
+@pytest.mark.parametrize("dist", ["binomial", "alpha0.25"])
+@pytest.mark.parametrize("m", [32, 256])
+def test_section64_distributions(m, dist):
+    """Section 6.4's non-uniform inputs (binomial B(m-1, 0.5), 0.25-uniform) with
+    delta buckets, keys and key-value, bit exact."""
+    n = (1 << 22) + 3
+    delta = float(np.float32(1000.0) / np.float32(m))
+    keys = (synthetic.binomial_f32(n, m, delta, 21) if dist == "binomial"
+            else synthetic.alpha_uniform_f32(n, m, delta, 0.25, 22))
+    case = Case(oracle.DELTA_F32, m, x0=0.0, delta=delta)
+    check_multisplit(keys, None, case)
+    check_multisplit(keys, synthetic.index_values(n), case)
