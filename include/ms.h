@@ -122,9 +122,9 @@ ms_status ms_histogram(const uint32_t *keys, size_t n, const ms_bucket_spec *spe
  *     capture.  It allocates nothing.
  *   - All calls share the array: calls that overlap on the GPU race and
  *     corrupt each other's results; serialize them (one stream, or events).
- *   - The scratch must hold 4*m*G + 16 bytes (G = CTAs of the launch, at
- *     most SMs x resident CTAs per SM; about 610 KiB at most on a 152-SM
- *     GB300).  A call needing more gets MS_ERR_OUT_OF_MEMORY and
+ *   - The scratch must hold 4*m*G + 16 bytes, plus 8*ceil(m*G/4096) for
+ *     m > 32 (G = CTAs of the launch, at most SMs x resident CTAs per SM;
+ *     about 610 KiB at most on a 152-SM GB300).  A call needing more gets MS_ERR_OUT_OF_MEMORY and
  *     nothing is enqueued.
  *   - Device-side failures (an expired bounded wait, a failed bounds check)
  *     are recorded in a word of the fixed array and are not reported by
@@ -225,8 +225,9 @@ ms_status ms_test_expire_lookback(void *stream);
  * otherwise).  A variant is: shape of the post-scan tile (0: 8 warps x 16
  * keys per lane, 1: 16 x 8, 2: 8 x 8), rank mode (0: warp ballots, allowed
  * for ceil(log2 m) <= 5; 1: per-warp peer tables; 2: per-thread bucket
- * counters with a 256-thread x 16-key tile, allowed for ceil(log2 m) <= 5,
- * shape ignored) and reorder (1: reorder each tile in shared memory before
+ * counters, allowed for ceil(log2 m) <= 5, with shape 0: 256 threads x 16
+ * keys, 1: the same with a 3-tile ring (keys only), 2: 256 threads x 8 keys)
+ * and reorder (1: reorder each tile in shared memory before
  * writing, 0: write from registers; 0 requires rank mode 0 and
  * ceil(log2 m) <= 3).  Unset entries use built-in defaults.  The tuner in
  * paper_1701_01189_gb300/autotune.py measures the candidates and sets the

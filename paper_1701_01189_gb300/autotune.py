@@ -23,7 +23,7 @@ DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.
 
 
 def variants(log2m: int):
-    out = [(0, 2, 1), (2, 2, 1)] if log2m <= 5 else []
+    out = [(0, 2, 1), (1, 2, 1), (2, 2, 1)] if log2m <= 5 else []
     for shape in (0, 1, 2):
         out.append((shape, 1, 1))
         if log2m <= 5:
@@ -100,3 +100,54 @@ def load(path: str = DEFAULT_PATH) -> int:
         st = B.ms_tune_set(e["kind"], e["pairs"], e["log2m"], e["size_class"], e["shape"], e["rank"], e["reorder"])
         count += st == B.MS_OK
     return count
+
+
+def tune_suite(n_log2s=(20, 26), ms=(2, 8, 32, 64, 256), kinds=("range", "delta", "mod", "radix"), reps: int = 5):
+    """Tunes every (identifier, m, keys or key-value, size) of the list on
+    seeded uniform inputs; returns the (key, variant) entries."""
+    import numpy as np
+    import torch
+
+    import synthetic
+
+    entries = []
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for n_log2 in n_log2s:
+        n = 1 << n_log2
+        u = torch.from_numpy(synthetic.uniform_u32(n, 1).view(np.int32)).to(dev)
+        f = torch.from_numpy(synthetic.uniform_f32_1000(n, 2).view(np.int32)).to(dev)
+        v = torch.arange(n, dtype=torch.int32, device=dev)
+        for kind in kinds:
+            for m in ms:
+                if kind == "radix":
+                    bits = (m - 1).bit_length()
+                    spec = B.BucketSpec.radix(32 - bits, bits)
+                elif kind == "range":
+                    spec = B.BucketSpec.range_u32(torch.from_numpy(synthetic.range_splitters(m, 3).view(np.int32)).to(dev))
+                elif kind == "mod":
+                    spec = B.BucketSpec.mod(m)
+                else:
+                    spec = B.BucketSpec.delta_f32(m, float(np.float32(1000.0) / np.float32(m)))
+                keys = f if kind == "delta" else u
+                for vals in (None, v):
+                    key, best, times = tune_workload(keys, vals, spec, reps=reps)
+                    entries.append((key, best))
+                    print(f"{kind} m={m} {'pairs' if vals is not None else 'keys'} n=2^{n_log2}: best {best} "
+                          f"{times[best]:.4f} ms of {len(times)} variants", flush=True)
+    return entries
+
+
+if __name__ == "__main__":
+    import argparse
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    ap = argparse.ArgumentParser(description="measure the multisplit kernel variants and save the fastest per workload")
+    ap.add_argument("--out", default=DEFAULT_PATH)
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+    from .build import build
+
+    build()
+    save(tune_suite(reps=args.reps), args.out)
+    print("saved", args.out)

@@ -11,9 +11,8 @@
 // (w, i, lane) sits at tile offset w*32*ITEMS + i*32 + lane, so that order is
 // the input order and the ranks below are stable.
 //
-// H holds one count per (bucket b, chunk c), stored chunk-major as H[c * m +
-// b]; one exclusive scan over it in bucket-major (row-vectorised) order yields
-// both global terms of Eq. 2.
+// H is bucket-major, H[b * G + c], so one exclusive scan over the
+// row-vectorised H yields both global terms of Eq. 2.
 //
 // GB300 budget: with ~22 bytes of HBM traffic per SM cycle to sustain, a
 // window of 32 keys may cost only ~37 warp instructions in the post-scan.
@@ -46,7 +45,7 @@ struct PostscanArgs {
   uint32_t tiles_per_cta;
   uint32_t num_tiles;
   uint32_t G;
-  const uint32_t* Gx;  // exclusive scan of row-vectorised H, stored chunk-major: Gx[c * m + b]
+  const uint32_t* Gx;  // exclusive scan of row-vectorised H (m*G entries)
   uint32_t* err;       // device status word
   uint32_t prefetch;   // 1: bulk-prefetch the next tiles into L2
   uint32_t reverse;    // 1: walk the chunk's tiles last to first
@@ -285,9 +284,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   build_bucket_tables<KIND, NB>(sp, s_tbl, s_lut);  // ends with a barrier
   pdl_wait();  // H scanned by the pre-scan grid
   // next global position of each bucket: chunk start (forward) or chunk end (reverse)
-  for (uint32_t b = threadIdx.x; b < m; b += THREADS) {  // Gx chunk-major: Gx[c * m + b]
-    const uint32_t next = (c + 1 < a.G) ? a.Gx[(size_t)(c + 1) * m + b] : (b + 1 < m ? a.Gx[b + 1] : a.n);
-    s_run[b] = a.reverse ? next : a.Gx[(size_t)c * m + b];
+  const uint32_t len = m * a.G;
+  for (uint32_t b = threadIdx.x; b < m; b += THREADS) {
+    const uint32_t e = b * a.G + c;
+    s_run[b] = a.reverse ? ((e + 1 < len) ? a.Gx[e + 1] : a.n) : a.Gx[e];
   }
   __syncthreads();
 

@@ -6,10 +6,11 @@
 // loops that forbid allocator calls on their hot path; and hosts whose device
 // memory is entirely handed out by another allocator (a framework's caching
 // pool), where a second allocator would fragment or oversubscribe it.  For
-// them, ms_multisplit_keys_noalloc runs the same pre-scan and post-scan
-// kernels as ms_multisplit_keys, with the scratch (histogram matrix, arrival
-// counter) taken from a fixed array in device memory that is part of the
-// loaded library instead of from the library's memory pool.
+// them, ms_multisplit_keys_noalloc runs the same kernels as
+// ms_multisplit_keys, with the scratch (histogram matrix, arrival counter or
+// look-back status words and ticket) taken from a fixed array in device
+// memory that is part of the loaded library instead of from the library's
+// memory pool.
 //
 // The array is a file-scope __device__ variable: every GPU on which the
 // library is loaded holds kStaticScratchBytes of it until the process exits.
@@ -20,7 +21,7 @@
 // stream capture.  All calls share the array: calls that overlap on the GPU
 // (concurrent streams, or several devices' worth of work racing on one device)
 // race on it and corrupt each other; serialize them.  Each call clears the
-// word that must start at zero (the arrival counter).
+// words that must start at zero (arrival counter, status words, ticket).
 #include <cstring>
 #include <mutex>
 
@@ -31,8 +32,9 @@ namespace ms {
 
 // 1 MiB: the first 256 bytes hold this entry point's device status word, the
 // rest the scratch.  The scratch needs 4*m*G bytes for the histogram matrix
-// (G = CTAs of the launch, at most SMs x resident CTAs per SM) plus 16 bytes;
-// on a 152-SM GB300 (G <= 4 * 152) that is at most about 610 KiB.
+// (G = CTAs of the launch, at most SMs x resident CTAs per SM) plus 16 bytes,
+// and for m > 32 8 bytes per 4096 matrix entries of look-back status; on a
+// 152-SM GB300 (G <= 4 * 152) that is at most about 610 KiB.
 constexpr size_t kStaticScratchBytes = (size_t)1 << 20;
 constexpr size_t kStaticHeader = 256;
 

@@ -80,10 +80,17 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   const uint32_t post_k = ch.K * (kTcTile / T);
   const uint32_t post_l = (uint32_t)(((uint64_t)c.n + T - 1) / T);
   const uint32_t m = c.sp.m;
+  // Up to 32 buckets the last pre-scan CTA scans H (a few rounds); beyond,
+  // H is longer and the separate look-back scan does it in parallel tiles.
+  const bool fused = m <= kTcMaxM;
+  const uint32_t len = m * ch.G;
+  const uint32_t nscan = fused ? 0u : (len + kScanTile - 1) / kScanTile;
 
-  // scratch: H (m * G words, 16-byte aligned) | arrival counter | (histogram only) offsets
-  const size_t h_bytes = ((size_t)m * ch.G * 4 + 15) & ~(size_t)15;
-  const size_t bytes = h_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
+  // scratch: H (m * G words, 16-byte aligned) | scan status (nscan u64) |
+  // arrival counter or ticket | (histogram only) offsets
+  const size_t h_bytes = ((size_t)len * 4 + 15) & ~(size_t)15;
+  const size_t st_bytes = (size_t)nscan * 8;
+  const size_t bytes = h_bytes + st_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
   void* ws = nullptr;
   cudaError_t e = cudaSuccess;
   if (c.ws_fixed != nullptr) {
@@ -94,19 +101,24 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
     if (e != cudaSuccess) return e;
   }
   uint32_t* H = static_cast<uint32_t*>(ws);
-  uint32_t* arrive = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes);
-  e = cudaMemsetAsync(arrive, 0, 16, c.stream);
+  auto* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + h_bytes);
+  uint32_t* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes);
+  e = cudaMemsetAsync(status, 0, st_bytes + 16, c.stream);
 
   const uint32_t aligned =
       ((reinterpret_cast<uintptr_t>(c.keys_in) | reinterpret_cast<uintptr_t>(c.vals_in)) & 15u) == 0;
   const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
   uint32_t* offsets = c.offsets;
-  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + 16);
+  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes + 16);
   if (e == cudaSuccess) {
-    e = launch_prescan<KIND>(c, ctx, ch, H, arrive, offsets);
+    e = launch_prescan<KIND>(c, ctx, ch, H, fused, ticket, offsets);
     trace_mark(slot, 1, c.stream);
-    trace_mark(slot, 2, c.stream);  // the global scan runs inside the pre-scan
   }
+  if (e == cudaSuccess && !fused) {
+    ScanArgs sa{H, len, ch.G, offsets, m, status, ticket, ctx.d_err};
+    e = launch_scan_lookback(sa, c.stream);
+  }
+  trace_mark(slot, 2, c.stream);
   if (e == cudaSuccess && c.counts != nullptr) {
     e = launch_counts_from_offsets(offsets, c.counts, m, c.stream);
     trace_mark(slot, 3, c.stream);

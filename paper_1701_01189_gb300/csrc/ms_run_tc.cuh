@@ -74,10 +74,11 @@ constexpr size_t kTcL2KeepBytes = (size_t)64 << 20;
 
 // The pre-scan of every design: `k_prescan_tc` (ms_tc.cuh) counting in
 // registers (m <= 8), per-thread counters (m <= 32) or per-lane byte counters
-// (m <= 256), its last CTA scanning H.  Chunks are whole 4096-key tiles.
+// (m <= 256); if `fused`, its last CTA scans H and writes the offsets.
+// Chunks are whole 4096-key tiles.
 template <int KIND>
-static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking& ch, uint32_t* H, uint32_t* arrive,
-                                  uint32_t* offsets) {
+static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking& ch, uint32_t* H, bool fused,
+                                  uint32_t* arrive, uint32_t* offsets) {
   const uint32_t m = c.sp.m;
   const int mode = m <= 8 ? kCountReg : m <= 32 ? kCountThread : kCountLaneBytes;
   // splitter lookup tables: 1024 cells x 8 copies (m <= 32), 2048 cells x 2 copies beyond
@@ -85,7 +86,8 @@ static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking&
   const bool vec = ((reinterpret_cast<uintptr_t>(c.keys_in)) & 15u) == 0;
   const size_t keep_tiles = kTcL2KeepBytes / ((size_t)kTcTile * 4);
   const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
-  TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, arrive, offsets, lb, lw, c.sp};
+  TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, fused ? 1u : 0u, arrive, offsets,
+               lb, lw, c.sp};
   static LaunchInfo li[3];
   if (mode == kCountLaneBytes) {
     auto k = k_prescan_tc<KIND, kCountLaneBytes>;
@@ -150,7 +152,7 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   uint32_t* offsets = c.offsets;
   if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + 16);
   if (e == cudaSuccess) {
-    e = launch_prescan<KIND>(c, ctx, ch, H, arrive, offsets);
+    e = launch_prescan<KIND>(c, ctx, ch, H, true, arrive, offsets);
     trace_mark(slot, 1, c.stream);
     trace_mark(slot, 2, c.stream);  // the global scan runs inside the pre-scan
   }
@@ -168,7 +170,8 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   return e != cudaSuccess ? e : e2;
 }
 
-// Variant shape 2 selects 8 keys per thread, any other 16.
+// Variant shape 2 selects 8 keys per thread, any other 16; shape 1 a
+// 3-slot ring for keys only (key-value pairs keep 2 slots).
 template <int KIND>
 static cudaError_t run_tc(const Call& c, DeviceCtx& ctx, int shape) {
   if (shape == 2) {
@@ -176,6 +179,7 @@ static cudaError_t run_tc(const Call& c, DeviceCtx& ctx, int shape) {
     return run_tc_cfg<KIND, false, 2, 8>(c, ctx);
   }
   if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2, 16>(c, ctx);
+  if (shape == 1) return run_tc_cfg<KIND, false, 3, 16>(c, ctx);
   return run_tc_cfg<KIND, false, 2, 16>(c, ctx);
 }
 

@@ -187,10 +187,9 @@ __device__ __forceinline__ void tc_fixup(const uint32_t (&key)[N], uint32_t (&bk
 }
 
 // ---------------------------------------------------------------------------
-// Pre-scan: per-chunk bucket histograms (column c of H, stored chunk-major as
-// H[c * m + b] so that a column is one coalesced write), then, in the last CTA
-// to finish, the exclusive scan of the row-vectorised (bucket-major) H in
-// place and the bucket offsets.
+// Pre-scan: per-chunk bucket histograms (column c of H, bucket-major
+// H[b * G + c]), then (fused, m <= 32) in the last CTA to finish the exclusive
+// scan of the row-vectorised H in place and the bucket offsets.
 struct TcPreArgs {
   const uint32_t* keys;
   uint32_t n;
@@ -199,7 +198,8 @@ struct TcPreArgs {
   uint32_t G;                // chunks (CTAs)
   uint32_t keep_from;        // chunk-relative tile index from which loads keep their lines in L2
   uint32_t vec;              // keys 16-byte aligned
-  uint32_t* H;               // m * G words, chunk-major H[c * m + b]; becomes the exclusive scan
+  uint32_t* H;               // m * G words, bucket-major H[b * G + c]; the exclusive scan if fused
+  uint32_t fused;            // 1: the last CTA to finish scans H and writes the offsets
   uint32_t* arrive;          // zero before the launch
   uint32_t* offsets;         // m + 1 words, or nullptr
   uint32_t lb, lw;           // lookup table: 2^lb cells, 2^lw copies (range buckets)
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
       uint32_t s2 = 0;
 #pragma unroll
       for (int ww = 0; ww < NW; ++ww) s2 += s_cnt[NW * m_pad * 8u + ww * m_pad + b];
-      a.H[(size_t)c * m + b] = s2;
+      a.H[(size_t)b * a.G + c] = s2;
     }
   } else {
     // column c of H: warp w sums buckets w, w+8, w+16, w+24 over the 256 threads
@@ -351,9 +351,10 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
       for (int k = 0; k < 8; ++k) s2 += row[36 * k];
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) s2 += __shfl_xor_sync(kFull, s2, d);
-      if (lane == 0) a.H[(size_t)c * m + b] = s2;
+      if (lane == 0) a.H[(size_t)b * a.G + c] = s2;
     }
   }
+  if (!a.fused) return;
   __threadfence();
   __syncthreads();
   if (t == 0) s_last = (atomicAdd(a.arrive, 1u) == a.G - 1u) ? 1u : 0u;
@@ -361,31 +362,35 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
   if (s_last == 0u) return;
   __threadfence();
 
-  // Last CTA: exclusive scan of H_row in place (Eq. 2) -- in bucket-major
-  // order, with H stored chunk-major -- and the bucket offsets.  Thread b
-  // owns bucket b: it sums its row (the G chunk counts, coalesced across the
-  // threads), one block scan of the row sums gives the buckets' bases, then it
-  // writes the running prefix of its row.  Two passes of G independent loads
-  // per thread instead of a serial walk over the matrix.
-  uint32_t row = 0;
-  if (t < m) {
-#pragma unroll 8
-    for (uint32_t cc = 0; cc < a.G; ++cc) row += __ldcg(a.H + (size_t)cc * m + t);
-  }
-  uint32_t total;
-  const uint32_t base = tc_block_scan(row, s_warp, &total);  // m <= 256 = threads
-  if (t < m) {
-    uint32_t run = base;
-#pragma unroll 8
-    for (uint32_t cc = 0; cc < a.G; ++cc) {
-      uint32_t* h = a.H + (size_t)cc * m + t;
-      const uint32_t v = __ldcg(h);
-      *h = run;
-      run += v;
+  // Last CTA: exclusive scan of H_row in place (Eq. 2), bucket offsets, in
+  // rounds of 4096 entries (a few rounds for m <= 32; larger m take the
+  // separate look-back scan, see `fused`)
+  const uint32_t len = m * a.G;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < len; base += kTcTile) {
+    uint32_t v[16];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t idx = base + 16u * t + i;
+      v[i] = idx < len ? __ldcg(a.H + idx) : 0u;
+      sum += v[i];
     }
-    if (a.offsets != nullptr) a.offsets[t] = base;
+    uint32_t total;
+    uint32_t run = carry + tc_block_scan(sum, s_warp, &total);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t idx = base + 16u * t + i;
+      if (idx < len) {
+        a.H[idx] = run;
+        if (a.offsets != nullptr && idx % a.G == 0u) a.offsets[idx / a.G] = run;
+      }
+      run += v[i];
+    }
+    carry += total;
+    __syncthreads();  // s_warp is rewritten by the next round
   }
-  if (t == 0 && a.offsets != nullptr) a.offsets[m] = total;
+  if (t == 0 && a.offsets != nullptr) a.offsets[m] = carry;
 }
 
 // ---------------------------------------------------------------------------
@@ -399,7 +404,7 @@ struct TcPostArgs {
   uint32_t tiles_per_cta;
   uint32_t num_tiles;
   uint32_t G;
-  const uint32_t* Gx;  // exclusive scan of row-vectorised H, stored chunk-major: Gx[c * m + b]
+  const uint32_t* Gx;  // exclusive scan of row-vectorised H (m * G entries)
   uint32_t* err;       // device status word
   uint32_t tma;        // 1: full tiles arrive by tensor copies (inputs 16-byte aligned)
   uint32_t lb, lw;     // lookup table: 2^lb cells, 2^lw copies (range buckets)
@@ -481,8 +486,11 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
     for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);  // inputs are not written by the pre-scan
   tc_build_tables<KIND>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
   pdl_wait();  // H scanned by the pre-scan grid
-  for (uint32_t b = t; b < m; b += kTcThreads)  // end of bucket b's share of this chunk (Gx chunk-major)
-    s_run[b] = (c + 1u < a.G) ? a.Gx[(size_t)(c + 1u) * m + b] : (b + 1u < m ? a.Gx[b + 1u] : a.n);
+  const uint32_t len = m * a.G;
+  for (uint32_t b = t; b < m; b += kTcThreads) {
+    const uint32_t e = b * a.G + c;
+    s_run[b] = (e + 1u < len) ? a.Gx[e + 1u] : a.n;  // end of bucket b's share of this chunk
+  }
   __syncthreads();
 
   uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)

@@ -55,7 +55,7 @@ def test_every_variant_matches_oracle(kind, m):
         ms.ms_tune_reset()
 
 
-@pytest.mark.parametrize("shape", [0, 2], ids=["16-per-thread", "8-per-thread"])
+@pytest.mark.parametrize("shape", [0, 1, 2], ids=["16-per-thread", "16-per-thread-3-slots", "8-per-thread"])
 @pytest.mark.parametrize("m", [2, 8, 32])
 def test_counter_variants_many_tiles_per_chunk(m, shape):
     """Per-thread-counter kernels at a size where every CTA walks many tiles
