@@ -73,3 +73,39 @@ def test_counter_variants_many_tiles_per_chunk(m, shape):
         check_multisplit(keys, synthetic.index_values(n), case)
     finally:
         ms.ms_tune_reset()
+
+
+def shipped_variants():
+    """(kind, log2m, shape, rank, reorder) of every entry of the shipped tuning table."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1701_01189_gb300",
+                        "tuning.json")
+    if not os.path.exists(path):
+        return []
+    out = set()
+    for e in json.load(open(path))["entries"]:
+        out.add((e["kind"], e["log2m"], e["shape"], e["rank"], e["reorder"]))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("entry", shipped_variants(), ids=lambda e: "k{}-lg{}-v{}{}{}".format(*e))
+def test_shipped_tuning_variants_many_tiles(entry):
+    """Every variant the shipped tuning table selects, at a size where every CTA
+    walks many tiles, bit exact against the oracle (keys and key-value)."""
+    import paper_1701_01189_gb300 as ms
+
+    kind, log2m, shape, rank, reorder = entry
+    m = 1 << log2m
+    name = {oracle.RANGE_U32: "range", oracle.MOD: "mod", oracle.RADIX: "radix", oracle.DELTA_F32: "delta"}[kind]
+    case = make_case(name, m)
+    n = (1 << 22) + 77
+    keys = synthetic.uniform_f32_1000(n, 13) if name == "delta" else synthetic.uniform_u32(n, 13)
+    try:
+        for pairs in (0, 1):
+            assert ms.ms_tune_set(case.kind, pairs, log2m, ms.ms_tune_size_class(n), shape, rank, reorder) == ms.MS_OK
+        check_multisplit(keys, None, case)
+        check_multisplit(keys, synthetic.index_values(n), case)
+    finally:
+        ms.ms_tune_reset()

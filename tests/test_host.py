@@ -132,3 +132,18 @@ def test_tuning_table_validation_and_defaults(lib):
     assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (2, 1, 1)
     ms.ms_tune_reset()
     assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (0, 2, 1)
+
+
+def test_shipped_tuning_table_is_valid(lib):
+    """Every entry of the shipped tuning table is a variant the library accepts."""
+    import json
+
+    from paper_1701_01189_gb300 import autotune
+
+    ms.ms_tune_reset()
+    try:
+        if os.path.exists(autotune.DEFAULT_PATH):
+            n = len(json.load(open(autotune.DEFAULT_PATH))["entries"])
+            assert autotune.load() == n > 0
+    finally:
+        ms.ms_tune_reset()
