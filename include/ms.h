@@ -226,8 +226,9 @@ ms_status ms_test_expire_lookback(void *stream);
  * keys per lane, 1: 16 x 8, 2: 8 x 8), rank mode (0: warp ballots, allowed
  * for ceil(log2 m) <= 5; 1: per-warp peer tables; 2: per-thread bucket
  * counters, allowed for ceil(log2 m) <= 5, with shape 0: 256 threads x 16
- * keys, 1: the same with a 3-tile ring (keys only), 2: 256 threads x 8 keys)
- * and reorder (1: reorder each tile in shared memory before
+ * keys, 1: the same with a 3-tile ring (keys only), 2: 256 threads x 8 keys;
+ * 3: peers found by eight ballots, per-warp bucket counters, any m) and
+ * reorder (1: reorder each tile in shared memory before
  * writing, 0: write from registers; 0 requires rank mode 0 and
  * ceil(log2 m) <= 3).  Unset entries use built-in defaults.  The tuner in
  * paper_1701_01189_gb300/autotune.py measures the candidates and sets the
@@ -236,6 +237,16 @@ int ms_tune_size_class(size_t n);
 ms_status ms_tune_set(int kind, int pairs, int log2m, int size_class, int shape, int rank, int reorder);
 ms_status ms_tune_get(int kind, int pairs, int log2m, int size_class, int *shape, int *rank, int *reorder);
 ms_status ms_tune_reset(void);
+
+/* How ms_radix_sort makes its passes, per keys-only / key-value (pairs 0/1)
+ * and size class: method 0 one-sweep kernels (each pass reads and writes the
+ * data once; tiles learn their digit offsets by decoupled look-back), 1 one
+ * three-stage multisplit per digit (pre-scan, scan, post-scan with the radix
+ * digit identifier; variants from the table above).  Unset entries use 0
+ * (n >= 2^30 always uses 1).  MS_ERR_INVALID_ARG for out-of-range arguments.
+ * ms_tune_reset clears these entries too. */
+ms_status ms_tune_set_sort(int pairs, int size_class, int method);
+ms_status ms_tune_get_sort(int pairs, int size_class, int *method);
 
 /* Human-readable name of a status code (static storage). */
 const char *ms_status_string(ms_status s);

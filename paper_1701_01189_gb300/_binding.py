@@ -87,7 +87,9 @@ def lib() -> ctypes.CDLL:
         L.ms_tune_set.argtypes = [I, I, I, I, I, I, I]
         L.ms_tune_get.argtypes = [I, I, I, I, P, P, P]
         L.ms_tune_reset.argtypes = []
-        for f in ("ms_tune_set", "ms_tune_get", "ms_tune_reset"):
+        L.ms_tune_set_sort.argtypes = [I, I, I]
+        L.ms_tune_get_sort.argtypes = [I, I, P]
+        for f in ("ms_tune_set", "ms_tune_get", "ms_tune_reset", "ms_tune_set_sort", "ms_tune_get_sort"):
             getattr(L, f).restype = ctypes.c_int
         L.ms_batch_plan_create.argtypes = [ctypes.POINTER(_Segment), ctypes.c_uint32, SP, ctypes.POINTER(P)]
         L.ms_batch_plan_create_dynamic.argtypes = [ctypes.c_uint32, ctypes.c_uint64, I, SP, ctypes.POINTER(P)]
@@ -174,6 +176,17 @@ def ms_tune_get(kind: int, pairs: int, log2m: int, size_class: int):
 
 def ms_tune_reset() -> int:
     return lib().ms_tune_reset()
+
+
+def ms_tune_set_sort(pairs: int, size_class: int, method: int) -> int:
+    return lib().ms_tune_set_sort(pairs, size_class, method)
+
+
+def ms_tune_get_sort(pairs: int, size_class: int) -> int:
+    """0: one-sweep passes, 1: three-stage multisplit passes."""
+    v = ctypes.c_int()
+    _check(lib().ms_tune_get_sort(pairs, size_class, ctypes.byref(v)), "ms_tune_get_sort")
+    return v.value
 
 
 def ms_status_string(status: int) -> str:

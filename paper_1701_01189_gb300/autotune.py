@@ -2,8 +2,9 @@
 
 For a set of workloads (bucket kind, m, keys or pairs, n) it times every
 variant the library offers -- post-scan tile shape (8 warps x 16 keys, 16 x 8,
-8 x 8), rank mode (warp ballots for m <= 32, per-warp peer tables, or
-per-thread bucket counters for m <= 32) and reordering (block reorder, or
+8 x 8), rank mode (warp ballots for m <= 32, per-warp peer tables,
+per-thread bucket counters for m <= 32, or ballot peers with per-warp
+counters) and reordering (block reorder, or
 direct writes for ballot ranks) -- with CUDA
 events on the current stream, and installs the fastest for that workload's key
 (kind, pairs, ceil(log2 m), size class of n) with ``ms_tune_set``.  Results can
@@ -26,6 +27,8 @@ def variants(log2m: int):
     out = [(0, 2, 1), (1, 2, 1), (2, 2, 1)] if log2m <= 5 else []
     for shape in (0, 1, 2):
         out.append((shape, 1, 1))
+        if log2m >= 4:
+            out.append((shape, 3, 1))
         if log2m <= 5:
             out.append((shape, 0, 1))
         if log2m <= 3:
@@ -49,9 +52,13 @@ def _time_call(fn, reps: int) -> float:
 
 def tune_workload(keys, vals, spec: B.BucketSpec, reps: int = 5):
     """Times every variant for this workload, installs the fastest, returns
-    (key, best_variant, {variant: ms})."""
+    (key, best_variant, {variant: ms}).  `keys` may be a list of key arrays of
+    one size (e.g. differently distributed inputs): a variant's time is then
+    the sum over them."""
     import torch
 
+    key_sets = keys if isinstance(keys, (list, tuple)) else [keys]
+    keys = key_sets[0]
     n = keys.numel()
     log2m = (spec.m - 1).bit_length()
     pairs = 1 if vals is not None else 0
@@ -63,30 +70,67 @@ def tune_workload(keys, vals, spec: B.BucketSpec, reps: int = 5):
     cs = spec.c()
     stream = torch.cuda.current_stream().cuda_stream
 
-    def run():
-        if vals is None:
-            st = B.ms_multisplit_keys(keys.data_ptr(), n, cs, ko.data_ptr(), off.data_ptr(), stream)
-        else:
-            st = B.ms_multisplit_pairs(keys.data_ptr(), vals.data_ptr(), n, cs, ko.data_ptr(), vo.data_ptr(),
-                                       off.data_ptr(), stream)
-        if st != B.MS_OK:
-            raise B.MsError(st, "autotune")
+    def runner(ks):
+        def run():
+            if vals is None:
+                st = B.ms_multisplit_keys(ks.data_ptr(), n, cs, ko.data_ptr(), off.data_ptr(), stream)
+            else:
+                st = B.ms_multisplit_pairs(ks.data_ptr(), vals.data_ptr(), n, cs, ko.data_ptr(), vo.data_ptr(),
+                                           off.data_ptr(), stream)
+            if st != B.MS_OK:
+                raise B.MsError(st, "autotune")
+        return run
 
     times = {}
     for v in variants(log2m):
         B._check(B.ms_tune_set(kind, pairs, log2m, sc, *v), "ms_tune_set")
-        times[v] = _time_call(run, reps)
+        times[v] = sum(_time_call(runner(ks), reps) for ks in key_sets)
     best = min(times, key=times.get)
     B._check(B.ms_tune_set(kind, pairs, log2m, sc, *best), "ms_tune_set")
     return (kind, pairs, log2m, sc), best, times
 
 
-def save(entries, path: str = DEFAULT_PATH):
-    """entries: list of (key, variant) pairs as returned by tune_workload."""
+def tune_sort(n: int, pairs: bool, reps: int = 3):
+    """Times ms_radix_sort (all 32 bits) with one-sweep passes (method 0) and with
+    three-stage multisplit passes (method 1, whose variants come from the
+    multisplit table, so tune that first); installs and returns the faster:
+    ((pairs, size_class), method, {method: ms})."""
+    import numpy as np
+    import torch
+
+    import synthetic
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keys = torch.from_numpy(synthetic.uniform_u32(n, 5).view(np.int32)).to(dev)
+    vals = torch.arange(n, dtype=torch.int32, device=dev) if pairs else None
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(keys) if pairs else None
+    stream = torch.cuda.current_stream().cuda_stream
+    sc = B.ms_tune_size_class(n)
+
+    def run():
+        st = B.ms_radix_sort(keys.data_ptr(), vals.data_ptr() if pairs else None, n, 0, 32, ko.data_ptr(),
+                             vo.data_ptr() if pairs else None, stream)
+        if st != B.MS_OK:
+            raise B.MsError(st, "autotune sort")
+
+    times = {}
+    for method in (0, 1):
+        B._check(B.ms_tune_set_sort(int(pairs), sc, method), "ms_tune_set_sort")
+        times[method] = _time_call(run, reps)
+    best = min(times, key=times.get)
+    B._check(B.ms_tune_set_sort(int(pairs), sc, best), "ms_tune_set_sort")
+    return (int(pairs), sc), best, times
+
+
+def save(entries, path: str = DEFAULT_PATH, sort_entries=()):
+    """entries: list of (key, variant) pairs as returned by tune_workload;
+    sort_entries: list of (key, method) pairs as returned by tune_sort."""
     data = [{"kind": k[0], "pairs": k[1], "log2m": k[2], "size_class": k[3], "shape": v[0], "rank": v[1],
              "reorder": v[2]} for k, v in entries]
+    sort = [{"pairs": k[0], "size_class": k[1], "method": m} for k, m in sort_entries]
     with open(path, "w") as f:
-        json.dump({"format": 1, "entries": data}, f, indent=1)
+        json.dump({"format": 1, "entries": data, "sort": sort}, f, indent=1)
 
 
 def load(path: str = DEFAULT_PATH) -> int:
@@ -99,6 +143,8 @@ def load(path: str = DEFAULT_PATH) -> int:
     for e in data.get("entries", []):
         st = B.ms_tune_set(e["kind"], e["pairs"], e["log2m"], e["size_class"], e["shape"], e["rank"], e["reorder"])
         count += st == B.MS_OK
+    for e in data.get("sort", []):
+        count += B.ms_tune_set_sort(e["pairs"], e["size_class"], e["method"]) == B.MS_OK
     return count
 
 
@@ -123,12 +169,15 @@ def tune_suite(n_log2s=(20, 26), ms=(2, 8, 32, 64, 256), kinds=("range", "delta"
                     bits = (m - 1).bit_length()
                     spec = B.BucketSpec.radix(32 - bits, bits)
                 elif kind == "range":
-                    spec = B.BucketSpec.range_u32(torch.from_numpy(synthetic.range_splitters(m, 3).view(np.int32)).to(dev))
+                    spl = synthetic.range_splitters(m, 3)
+                    spec = B.BucketSpec.range_u32(torch.from_numpy(spl.view(np.int32)).to(dev))
                 elif kind == "mod":
                     spec = B.BucketSpec.mod(m)
                 else:
                     spec = B.BucketSpec.delta_f32(m, float(np.float32(1000.0) / np.float32(m)))
                 keys = f if kind == "delta" else u
+                if kind == "range":  # the benchmark's range inputs: uniform and skewed keys
+                    keys = [u, torch.from_numpy(synthetic.skewed_u32(n, spl, 4).view(np.int32)).to(dev)]
                 for vals in (None, v):
                     key, best, times = tune_workload(keys, vals, spec, reps=reps)
                     entries.append((key, best))
@@ -149,5 +198,13 @@ if __name__ == "__main__":
     from .build import build
 
     build()
-    save(tune_suite(reps=args.reps), args.out)
+    entries = tune_suite(reps=args.reps)
+    sort_entries = []
+    for n_log2 in (22, 28):
+        for pairs in (False, True):
+            key, best, times = tune_sort(1 << n_log2, pairs)
+            sort_entries.append((key, best))
+            print(f"sort n=2^{n_log2} {'pairs' if pairs else 'keys'}: best method {best} "
+                  f"({', '.join(f'{k}: {v:.3f} ms' for k, v in times.items())})", flush=True)
+    save(entries, args.out, sort_entries)
     print("saved", args.out)

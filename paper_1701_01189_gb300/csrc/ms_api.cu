@@ -265,10 +265,11 @@ extern "C" ms_status ms_radix_sort(const uint32_t* keys_in, const uint32_t* vals
     if (e == cudaSuccess && pairs) e = cudaMemcpyAsync(vals_out, vals_in, bytes, cudaMemcpyDeviceToDevice, s);
     return to_status(e);
   }
-  if (n < ((size_t)1 << 30))
+  if (n < ((size_t)1 << 30) && choose_sort_method((uint32_t)n, pairs) == 0)
     return to_status(run_onesweep_sort(keys_in, pairs ? vals_in : nullptr, (uint32_t)n, begin_bit, end_bit, keys_out,
                                        pairs ? vals_out : nullptr, s, *ctx));
-  // n >= 2^30: one three-stage multisplit per digit
+  // one three-stage multisplit per digit (tuned, or n >= 2^30, beyond the
+  // one-sweep kernels' 30-bit status counts)
   const int passes = (width + 7) / 8;
   void* tmp = nullptr;
   uint32_t* tmp_k = nullptr;

@@ -27,8 +27,9 @@ constexpr uint32_t kDevErrBounds = 2u;   // an index failed its bounds check (th
 enum Kind : int { kRange = 0, kDelta = 1, kRadix = 2, kMod = 3 };
 
 // How the post-scan ranks keys: ballot voting or peer tables inside each
-// warp, or per-thread bucket counters (m <= 32; ms_tc.cuh).
-enum RankMode : int { kRankBallot = 0, kRankTable = 1, kRankThread = 2 };
+// warp, per-thread bucket counters (m <= 32; ms_tc.cuh), or peers found by
+// ballots with per-warp bucket counters in shared memory (any m).
+enum RankMode : int { kRankBallot = 0, kRankTable = 1, kRankThread = 2, kRankVote = 3 };
 
 // Bucket identifier parameters as the kernels see them (built by the host
 // from an ms_bucket_spec).

@@ -50,6 +50,9 @@ struct Variant {
 int size_class(uint32_t n);
 // The tuned (or default) variant for a request (ms_tune.cu).
 Variant choose_variant(const Call& c);
+// How the radix sort makes its passes: 0 one-sweep kernels, 1 three-stage
+// multisplits with the radix-digit identifier (ms_tune.cu).
+int choose_sort_method(uint32_t n, bool pairs);
 
 // Runs the three stages for one request.  Defined per bucket kind in
 // ms_kind_<kind>.cu.

@@ -103,7 +103,7 @@ __device__ __forceinline__ void rank_windows(const uint32_t* wk, uint32_t avail,
                                              const uint32_t* s_tbl, const uint2* s_lut, uint32_t* wc,
                                              uint32_t* wpeer, uint32_t m_pad, uint32_t m, const uint32_t* lane_x,
                                              uint32_t lt_mask, uint32_t lane, uint32_t (&rb)[ITEMS]) {
-  if constexpr (RANK == kRankTable) {
+  if constexpr (RANK == kRankTable || RANK == kRankVote) {
     for (uint32_t b = lane; b < m_pad; b += 32) wc[b] = 0u;
     __syncwarp();
   }
@@ -127,6 +127,23 @@ __device__ __forceinline__ void rank_windows(const uint32_t* wk, uint32_t avail,
       const uint32_t before = __shfl_sync(kFull, run, b & 31u);
       rb[i] = (before + __popc(own & lt_mask)) | (b << 16);
       run += __popc(lane_bm);
+    } else if constexpr (RANK == kRankVote) {
+      // Section 5.4's voting for any m: NB ballots give every lane the mask
+      // of the lanes whose bucket equals its own (no shared memory, so no
+      // conflicts however skewed the buckets); the lowest of them advances
+      // the warp's counter of the bucket by the group's size.
+      const uint32_t vb = FULL ? kFull : __ballot_sync(kFull, valid);
+      uint32_t own = vb;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const uint32_t bal = __ballot_sync(kFull, (b >> k) & 1u);
+        own &= ((b >> k) & 1u) ? bal : ~bal;
+      }
+      const uint32_t lt = own & lt_mask;
+      uint32_t before = 0;
+      if (valid && lt == 0u) before = atomicAdd(wc + b, (uint32_t)__popc(own));
+      before = __shfl_sync(kFull, before, (__ffs(own) - 1) & 31);
+      rb[i] = (before + __popc(lt)) | (b << 16);
     } else {
       // peer table (two, alternating by window): OR the lane bit into the
       // bucket's entry, read the peers back; the lowest peer advances the
@@ -229,7 +246,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   constexpr uint32_t T = Lay::T;
   static_assert(NW >= 8, "the per-bucket phase needs >= 256 threads");
   static_assert(NW == 8 || NW == 16 || NW == 32, "NW must be 8, 16 or 32");
-  static_assert(RANK == kRankTable || NB <= 5, "ballot ranks need m <= 32");
+  static_assert(RANK != kRankBallot || NB <= 5, "lane-histogram ballot ranks need m <= 32");
   static_assert(STAGES >= 1 && STAGES <= 4, "1..4 ring slots");
   extern __shared__ __align__(16) uint32_t smem[];
   const DevSpec& sp = a.sp;

@@ -125,7 +125,7 @@ struct OsLayout {
 // always ends); once a tile's prefixes are published, the CTA takes its next
 // ticket and copies that tile into the other slot while it reorders and
 // writes the current one.
-template <bool PAIRS>
+template <bool PAIRS, int RANK>
 __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(OnesweepArgs a) {
   using Lay = OsLayout<PAIRS>;
   constexpr uint32_t T = Lay::T;
@@ -206,11 +206,11 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
     const uint32_t avail = tile_n - min(tile_n, w * (32u * kOsItems));
     uint32_t rb[kOsItems];
     if (tile_n == T)
-      rank_windows<kRadix, 8, kOsItems, kRankTable, true>(sk + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad, m,
-                                                         lane_x, lanemask_lt(), lane, rb);
+      rank_windows<kRadix, 8, kOsItems, RANK, true>(sk + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad, m,
+                                                   lane_x, lanemask_lt(), lane, rb);
     else
-      rank_windows<kRadix, 8, kOsItems, kRankTable, false>(sk + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad,
-                                                          m, lane_x, lanemask_lt(), lane, rb);
+      rank_windows<kRadix, 8, kOsItems, RANK, false>(sk + off0, avail, sp, nullptr, nullptr, wc, wpeer, m_pad,
+                                                    m, lane_x, lanemask_lt(), lane, rb);
     if (__syncthreads_or(!ok)) {
       // a copy never arrived (the error bit is set): drain the copies in flight, stop
       if (threadIdx.x == 0)
@@ -356,15 +356,15 @@ cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, 
     const int d = ctx.device & 63;
     if (!((ready >> d) & 1ull)) {
       cudaFuncSetAttribute(k_radix_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, kHistNW * 4 * 256 * 4);
-      cudaFuncSetAttribute(k_onesweep_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)OsLayout<false>::kBytes);
-      cudaFuncSetAttribute(k_onesweep_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)OsLayout<true>::kBytes);
+      for (auto k : {k_onesweep_pass<false, kRankTable>, k_onesweep_pass<false, kRankVote>})
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OsLayout<false>::kBytes);
+      for (auto k : {k_onesweep_pass<true, kRankTable>, k_onesweep_pass<true, kRankVote>})
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OsLayout<true>::kBytes);
       int v = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_onesweep_pass<false>, kOsNW * 32,
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_onesweep_pass<false, kRankTable>, kOsNW * 32,
                                                         OsLayout<false>::kBytes) == cudaSuccess && v > 0)
         g_occ[d][0] = v;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_onesweep_pass<true>, kOsNW * 32,
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_onesweep_pass<true, kRankTable>, kOsNW * 32,
                                                         OsLayout<true>::kBytes) == cudaSuccess && v > 0)
         g_occ[d][1] = v;
       ready |= 1ull << d;
@@ -382,6 +382,15 @@ cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, 
   const uint32_t aligned = ((reinterpret_cast<uintptr_t>(keys_in) | reinterpret_cast<uintptr_t>(vals_in) |
                              reinterpret_cast<uintptr_t>(keys_out) | reinterpret_cast<uintptr_t>(vals_out) |
                              reinterpret_cast<uintptr_t>(tmp_k) | reinterpret_cast<uintptr_t>(tmp_v)) & 15u) == 0;
+  // ranks of the 8-bit digits: peer tables or ballot peers, as the tuning
+  // table says for radix-digit multisplits with 256 buckets at this size
+  Call probe;
+  std::memset(&probe, 0, sizeof probe);
+  probe.kind = kRadix;
+  probe.sp.nbits = 8;
+  probe.n = n;
+  probe.vals_in = vals_in;
+  const bool vote = choose_variant(probe).rank == kRankVote;
   const uint32_t* src_k = keys_in;
   const uint32_t* src_v = vals_in;
   for (uint32_t p = 0; p < passes && e == cudaSuccess; ++p) {
@@ -409,10 +418,14 @@ cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, 
     oa.err = ctx.d_err;
     oa.aligned = aligned;
     const uint32_t grid = std::max(1u, std::min(L, (uint32_t)ctx.sm_count * (uint32_t)(pairs ? occ_pairs : occ_keys)));
-    if (pairs)
-      k_onesweep_pass<true><<<grid, kOsNW * 32, OsLayout<true>::kBytes, s>>>(oa);
+    if (pairs && vote)
+      k_onesweep_pass<true, kRankVote><<<grid, kOsNW * 32, OsLayout<true>::kBytes, s>>>(oa);
+    else if (pairs)
+      k_onesweep_pass<true, kRankTable><<<grid, kOsNW * 32, OsLayout<true>::kBytes, s>>>(oa);
+    else if (vote)
+      k_onesweep_pass<false, kRankVote><<<grid, kOsNW * 32, OsLayout<false>::kBytes, s>>>(oa);
     else
-      k_onesweep_pass<false><<<grid, kOsNW * 32, OsLayout<false>::kBytes, s>>>(oa);
+      k_onesweep_pass<false, kRankTable><<<grid, kOsNW * 32, OsLayout<false>::kBytes, s>>>(oa);
     e = cudaGetLastError();
     src_k = dst_k;
     src_v = dst_v;

@@ -68,7 +68,7 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   static_assert(kTcTile % T == 0, "post-scan tiles divide the pre-scan's");
   auto kpost = k_postscan<KIND, NB, NW, ITEMS, PAIRS, RANK, REORDER, MINB, STAGES>;
   const uint32_t m_pad = c.sp.m_pad, lb = c.sp.lut_bits;
-  const uint32_t mp_max = RANK == kRankBallot ? 32u : 256u;
+  const uint32_t mp_max = RANK == kRankBallot ? 32u : 256u;  // peer tables and vote counters: any m
   const size_t smem_post_max = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>(mp_max, 11);
   const size_t smem_post = postscan_smem_bytes<KIND, NW, ITEMS, PAIRS, RANK, REORDER, STAGES>(m_pad, lb);
   static LaunchInfo li_post;
@@ -103,7 +103,7 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   uint32_t* H = static_cast<uint32_t*>(ws);
   auto* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + h_bytes);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes);
-  e = cudaMemsetAsync(status, 0, st_bytes + 16, c.stream);
+  e = cudaMemsetAsync(ws, 0, h_bytes + st_bytes + 16, c.stream);  // H (the pre-scan adds into it), status, counter
 
   const uint32_t aligned =
       ((reinterpret_cast<uintptr_t>(c.keys_in) | reinterpret_cast<uintptr_t>(c.vals_in)) & 15u) == 0;
@@ -163,6 +163,7 @@ template <int KIND>
 static cudaError_t run_ms_kind(const Call& c, DeviceCtx& ctx) {
   const Variant v = choose_variant(c);
   if (v.rank == kRankThread && c.sp.m <= kTcMaxM) return run_tc<KIND>(c, ctx, v.shape);
+  if (v.rank == kRankVote) return run_ms_pairs<KIND, 8, kRankVote, 1>(c, ctx, v.shape);
   if (v.rank == kRankBallot && c.sp.nbits <= 5) {
     switch (c.sp.nbits) {
       case 0: return run_ms_ballot<KIND, 0>(c, ctx, v);

@@ -86,25 +86,27 @@ static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking&
   const bool vec = ((reinterpret_cast<uintptr_t>(c.keys_in)) & 15u) == 0;
   const size_t keep_tiles = kTcL2KeepBytes / ((size_t)kTcTile * 4);
   const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
-  TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, fused ? 1u : 0u, arrive, offsets,
-               lb, lw, c.sp};
+  TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, 1u, ch.K - keep, vec ? 1u : 0u, H, fused ? 1u : 0u, arrive,
+               offsets, lb, lw, c.sp};
   static LaunchInfo li[3];
-  if (mode == kCountLaneBytes) {
-    auto k = k_prescan_tc<KIND, kCountLaneBytes>;
-    const size_t smem = tc_prescan_smem<KIND, kCountLaneBytes>(m, lb, lw);
-    setup_kernel(li[2], k, kTcThreads, tc_prescan_smem<KIND, kCountLaneBytes>(kMaxM, lb, lw), smem, ctx.device);
-    k<<<ch.G, kTcThreads, smem, c.stream>>>(pa);
-  } else if (mode == kCountThread) {
-    auto k = k_prescan_tc<KIND, kCountThread>;
-    const size_t smem = tc_prescan_smem<KIND, kCountThread>(m, lb, lw);
-    setup_kernel(li[0], k, kTcThreads, tc_prescan_smem<KIND, kCountThread>(kTcMaxM, lb, lw), smem, ctx.device);
-    k<<<ch.G, kTcThreads, smem, c.stream>>>(pa);
-  } else {
-    auto k = k_prescan_tc<KIND, kCountReg>;
-    const size_t smem = tc_prescan_smem<KIND, kCountReg>(m, lb, lw);
-    setup_kernel(li[1], k, kTcThreads, tc_prescan_smem<KIND, kCountReg>(kTcMaxM, lb, lw), smem, ctx.device);
-    k<<<ch.G, kTcThreads, smem, c.stream>>>(pa);
-  }
+  // enough CTAs to fill the SMs: a chunk (one post-scan CTA's work) is split
+  // into `sub` runs of tiles when the post-scan has fewer CTAs than the
+  // pre-scan can keep resident
+  auto launch = [&](auto k, size_t smem, size_t smem_max, LaunchInfo& info) {
+    const int resident = setup_kernel(info, k, kTcThreads, smem_max, smem, ctx.device);
+    const uint32_t want = (uint32_t)(ctx.sm_count * resident);
+    pa.sub = std::max(1u, std::min(ch.K, want / ch.G));  // one wave: a partial second wave only adds a tail
+    k<<<ch.G * pa.sub, kTcThreads, smem, c.stream>>>(pa);
+  };
+  if (mode == kCountLaneBytes)
+    launch(k_prescan_tc<KIND, kCountLaneBytes>, tc_prescan_smem<KIND, kCountLaneBytes>(m, lb, lw),
+           tc_prescan_smem<KIND, kCountLaneBytes>(kMaxM, lb, lw), li[2]);
+  else if (mode == kCountThread)
+    launch(k_prescan_tc<KIND, kCountThread>, tc_prescan_smem<KIND, kCountThread>(m, lb, lw),
+           tc_prescan_smem<KIND, kCountThread>(kTcMaxM, lb, lw), li[0]);
+  else
+    launch(k_prescan_tc<KIND, kCountReg>, tc_prescan_smem<KIND, kCountReg>(m, lb, lw),
+           tc_prescan_smem<KIND, kCountReg>(kTcMaxM, lb, lw), li[1]);
   return cudaGetLastError();
 }
 
@@ -140,7 +142,7 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   }
   uint32_t* H = static_cast<uint32_t*>(ws);
   uint32_t* arrive = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes);
-  e = cudaMemsetAsync(arrive, 0, 16, c.stream);
+  e = cudaMemsetAsync(ws, 0, h_bytes + 16, c.stream);  // H (the pre-scan adds into it) and the counter
 
   CUtensorMap tmk, tmv;
   std::memset(&tmk, 0, sizeof tmk);

@@ -195,10 +195,12 @@ struct TcPreArgs {
   uint32_t n;
   uint32_t tiles_per_chunk;  // K
   uint32_t num_tiles;        // L
-  uint32_t G;                // chunks (CTAs)
+  uint32_t G;                // chunks
+  uint32_t sub;              // CTAs per chunk (G * sub CTAs), each counting a run of the chunk's tiles
   uint32_t keep_from;        // chunk-relative tile index from which loads keep their lines in L2
   uint32_t vec;              // keys 16-byte aligned
-  uint32_t* H;               // m * G words, bucket-major H[b * G + c]; the exclusive scan if fused
+  uint32_t* H;               // m * G words, bucket-major H[b * G + c], zero before the launch (the parts
+                             // of a chunk add their counts); the exclusive scan if fused
   uint32_t fused;            // 1: the last CTA to finish scans H and writes the offsets
   uint32_t* arrive;          // zero before the launch
   uint32_t* offsets;         // m + 1 words, or nullptr
@@ -244,9 +246,13 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
   uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // kCountThread/kCountReg: counter (bucket 0, thread t)
   uint32_t* wwords = s_cnt + w * m_pad * 8u;   // kCountLaneBytes: this warp's byte counters
   uint32_t* wtot = s_cnt + NW * m_pad * 8u + w * m_pad;  // ... and its 32-bit totals
-  const uint32_t c = blockIdx.x;
-  const uint32_t t0 = c * a.tiles_per_chunk;
-  const uint32_t t1 = min(t0 + a.tiles_per_chunk, a.num_tiles);
+  // CTA (c, part): part `part` of the `sub` parts of chunk c
+  const uint32_t c = blockIdx.x / a.sub, part = blockIdx.x % a.sub;
+  const uint32_t c0 = c * a.tiles_per_chunk;  // first tile of the chunk
+  const uint32_t c1 = min(c0 + a.tiles_per_chunk, a.num_tiles);
+  const uint32_t per = (a.tiles_per_chunk + a.sub - 1) / a.sub;
+  const uint32_t t0 = min(c0 + part * per, c1);
+  const uint32_t t1 = min(t0 + per, c1);
   const uint32_t nfull = a.n / kTcTile;  // tiles [0, nfull) are full
   const uint32_t tv1 = a.vec ? max(t0, min(t1, nfull)) : t0;
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
   };
   // thread (w, lane) holds words w*512 + j*128 + 4*lane + e of the tile
   auto load16 = [&](uint32_t (&key)[16], uint32_t tile) {
-    const uint64_t pol = (tile - t0 >= a.keep_from) ? pol_last : pol_first;
+    const uint64_t pol = (tile - c0 >= a.keep_from) ? pol_last : pol_first;
     const uint32_t* src = a.keys + (size_t)tile * kTcTile + w * 512u + 4u * lane;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -340,7 +346,7 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
       uint32_t s2 = 0;
 #pragma unroll
       for (int ww = 0; ww < NW; ++ww) s2 += s_cnt[NW * m_pad * 8u + ww * m_pad + b];
-      a.H[(size_t)b * a.G + c] = s2;
+      if (s2) atomicAdd(a.H + (size_t)b * a.G + c, s2);
     }
   } else {
     // column c of H: warp w sums buckets w, w+8, w+16, w+24 over the 256 threads
@@ -351,13 +357,13 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
       for (int k = 0; k < 8; ++k) s2 += row[36 * k];
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) s2 += __shfl_xor_sync(kFull, s2, d);
-      if (lane == 0) a.H[(size_t)b * a.G + c] = s2;
+      if (lane == 0 && s2) atomicAdd(a.H + (size_t)b * a.G + c, s2);
     }
   }
   if (!a.fused) return;
   __threadfence();
   __syncthreads();
-  if (t == 0) s_last = (atomicAdd(a.arrive, 1u) == a.G - 1u) ? 1u : 0u;
+  if (t == 0) s_last = (atomicAdd(a.arrive, 1u) == a.G * a.sub - 1u) ? 1u : 0u;
   __syncthreads();
   if (s_last == 0u) return;
   __threadfence();

@@ -15,6 +15,9 @@ constexpr int kKinds = 4, kNbits = 9, kClasses = 4;
 std::mutex g_mu;
 bool g_set[kKinds][2][kNbits][kClasses] = {};
 Variant g_table[kKinds][2][kNbits][kClasses];
+// radix sort passes per (pairs, size class): 0 one-sweep, 1 three-stage multisplits
+bool g_sort_set[2][kClasses] = {};
+int g_sort[2][kClasses];
 
 // Up to 32 buckets: per-thread bucket counters (ms_tc.cuh).  Beyond, peer
 // tables with block reordering; key-value pairs prefer the smaller 8 x 8 tile
@@ -41,6 +44,12 @@ int size_class(uint32_t n) {
   return 3;
 }
 
+int choose_sort_method(uint32_t n, bool pairs) {
+  const int sc = size_class(n), p = pairs ? 1 : 0;
+  std::lock_guard<std::mutex> lock(g_mu);
+  return g_sort_set[p][sc] ? g_sort[p][sc] : 0;
+}
+
 Variant choose_variant(const Call& c) {
   const int nb = (int)c.sp.nbits, pairs = c.vals_in != nullptr ? 1 : 0, sc = size_class(c.n);
   std::lock_guard<std::mutex> lock(g_mu);
@@ -56,7 +65,7 @@ extern "C" int ms_tune_size_class(size_t n) { return n >= ((size_t)1 << 32) ? 3 
 
 extern "C" ms_status ms_tune_set(int kind, int pairs, int nbits, int sclass, int shape, int rank, int reorder) {
   if (kind < 0 || kind >= kKinds || pairs < 0 || pairs > 1 || nbits < 0 || nbits >= kNbits || sclass < 0 ||
-      sclass >= kClasses || shape < 0 || shape > 2 || rank < 0 || rank > 2 || reorder < 0 || reorder > 1)
+      sclass >= kClasses || shape < 0 || shape > 2 || rank < 0 || rank > 3 || reorder < 0 || reorder > 1)
     return MS_ERR_INVALID_ARG;
   if ((rank == kRankBallot || rank == kRankThread) && nbits > 5) return MS_ERR_INVALID_ARG;
   if (reorder == 0 && (rank != kRankBallot || nbits > 3)) return MS_ERR_INVALID_ARG;
@@ -87,5 +96,23 @@ extern "C" ms_status ms_tune_reset(void) {
     for (auto& b : a)
       for (auto& c : b)
         for (auto& d : c) d = false;
+  for (auto& a : g_sort_set)
+    for (auto& b : a) b = false;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_tune_set_sort(int pairs, int sclass, int method) {
+  if (pairs < 0 || pairs > 1 || sclass < 0 || sclass >= kClasses || method < 0 || method > 1)
+    return MS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_sort[pairs][sclass] = method;
+  g_sort_set[pairs][sclass] = true;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_tune_get_sort(int pairs, int sclass, int* method) {
+  if (pairs < 0 || pairs > 1 || sclass < 0 || sclass >= kClasses) return MS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (method) *method = g_sort_set[pairs][sclass] ? g_sort[pairs][sclass] : 0;
   return MS_OK;
 }

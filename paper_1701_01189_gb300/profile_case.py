@@ -56,11 +56,13 @@ def main(argv=None):
     else:
         spec = ms.BucketSpec.delta_f32(args.m, float(np.float32(1000.0) / np.float32(args.m)))
     cs = spec.c()
-    if args.variant is not None and args.kind != "sort":
+    if args.variant is not None:
+        # for a sort, the variant of radix-digit multisplits with 256 buckets (its ranks)
         shape, rank, reorder = (int(x) for x in args.variant.split(","))
-        log2m = (args.m - 1).bit_length()
+        log2m = 8 if args.kind == "sort" else (args.m - 1).bit_length()
+        kind = ms.RADIX if args.kind == "sort" else spec.kind
         for pairs in (0, 1):
-            st = ms.ms_tune_set(spec.kind, pairs, log2m, ms.ms_tune_size_class(n), shape, rank, reorder)
+            st = ms.ms_tune_set(kind, pairs, log2m, ms.ms_tune_size_class(n), shape, rank, reorder)
             if st != ms.MS_OK:
                 raise ms.MsError(st, "ms_tune_set")
 

@@ -88,3 +88,47 @@ def test_config_2p28(pairs):
         assert np.all(gv[1:][same] > gv[:-1][same])  # stable among equal keys
     else:
         np.testing.assert_array_equal(gk, np.sort(keys))
+
+
+@pytest.mark.parametrize("rank", [1, 3], ids=["peer-tables", "ballot-peers"])
+@pytest.mark.parametrize("n", [4097, (1 << 20) + 5, (1 << 22) + 3])
+def test_sort_rank_modes(rank, n):
+    """Both ways the one-sweep passes can rank 8-bit digits (selected by the
+    tuning entry of radix-digit multisplits with 256 buckets), keys and pairs."""
+    import paper_1701_01189_gb300 as ms
+
+    keys = synthetic.uniform_u32(n, 71)
+    vals = synthetic.index_values(n)
+    try:
+        for pairs in (0, 1):
+            assert ms.ms_tune_set(ms.RADIX, pairs, 8, ms.ms_tune_size_class(n), 0, rank, 1) == ms.MS_OK
+        ek, ev = oracle.radix_sort(keys, vals, 0, 32)
+        gk, gv = gpu_sort(keys, vals, 0, 32)
+        np.testing.assert_array_equal(gk, ek)
+        np.testing.assert_array_equal(gv, ev)
+        gk2, _ = gpu_sort(keys, None, 0, 32)
+        np.testing.assert_array_equal(gk2, ek)
+    finally:
+        ms.ms_tune_reset()
+
+
+@pytest.mark.parametrize("bits", [(0, 32), (0, 16), (3, 30)])
+@pytest.mark.parametrize("n", [1, 4097, (1 << 20) + 5, (1 << 22) + 3])
+def test_sort_by_multisplit_passes(bits, n):
+    """The sort made of three-stage multisplit passes (tuning method 1), keys
+    and pairs, against the oracle."""
+    import paper_1701_01189_gb300 as ms
+
+    keys = synthetic.uniform_u32(n, 91)
+    vals = synthetic.index_values(n)
+    try:
+        for pairs in (0, 1):
+            assert ms.ms_tune_set_sort(pairs, ms.ms_tune_size_class(n), 1) == ms.MS_OK
+        ek, ev = oracle.radix_sort(keys, vals, *bits)
+        gk, gv = gpu_sort(keys, vals, *bits)
+        np.testing.assert_array_equal(gk, ek)
+        np.testing.assert_array_equal(gv, ev)
+        gk2, _ = gpu_sort(keys, None, *bits)
+        np.testing.assert_array_equal(gk2, ek)
+    finally:
+        ms.ms_tune_reset()

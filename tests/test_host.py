@@ -132,6 +132,11 @@ def test_tuning_table_validation_and_defaults(lib):
     assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (2, 1, 1)
     ms.ms_tune_reset()
     assert ms.ms_tune_get(ms.MOD, 0, 5, 3) == (0, 2, 1)
+    assert ms.ms_tune_get_sort(1, 3) == 0  # one-sweep passes by default
+    assert ms.ms_tune_set_sort(1, 3, 1) == ms.MS_OK and ms.ms_tune_get_sort(1, 3) == 1
+    assert ms.ms_tune_set_sort(1, 3, 2) == ms.MS_ERR_INVALID_ARG and ms.ms_tune_set_sort(2, 3, 1) == ms.MS_ERR_INVALID_ARG
+    ms.ms_tune_reset()
+    assert ms.ms_tune_get_sort(1, 3) == 0
 
 
 def test_shipped_tuning_table_is_valid(lib):
@@ -143,7 +148,8 @@ def test_shipped_tuning_table_is_valid(lib):
     ms.ms_tune_reset()
     try:
         if os.path.exists(autotune.DEFAULT_PATH):
-            n = len(json.load(open(autotune.DEFAULT_PATH))["entries"])
+            d = json.load(open(autotune.DEFAULT_PATH))
+            n = len(d["entries"]) + len(d.get("sort", []))
             assert autotune.load() == n > 0
     finally:
         ms.ms_tune_reset()
