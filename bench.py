@@ -449,6 +449,58 @@ def extras_gpu(args, ms, metrics, torch, dev):
         del keys, vals, ko, vo
     torch.cuda.empty_cache()
 
+    # radix width r = 4..8 (Section 6.3's sort table): n = 2^25, all 32 bits, ceil(32 / r) passes
+    n = 1 << 25
+    keys = dev_u32(synthetic.uniform_u32(n, 9))
+    vals = dev_u32(synthetic.uniform_u32(n, 10))
+    ko, vo = torch.empty_like(keys), torch.empty_like(keys)
+    sptr = torch.cuda.current_stream().cuda_stream
+    for pairs in (False, True):
+        for r in (4, 5, 6, 7, 8):
+            def run_r():
+                st = ms.ms_radix_sort_r(keys.data_ptr(), vals.data_ptr() if pairs else None, n, 0, 32, r,
+                                        ko.data_ptr(), vo.data_ptr() if pairs else None, sptr)
+                if st != ms.MS_OK:
+                    raise ms.MsError(st, f"sort r={r}")
+
+            t = _time(torch, run_r, reps=5)
+            rate = metrics.rate_g(n, t * 1e-3)
+            out[f"sort_r{r}_2p25_{'pairs' if pairs else 'keys'}"] = {
+                "ms": round(t, 4), ("gpairs_s" if pairs else "gkeys_s"): round(rate, 2), "passes": (32 + r - 1) // r}
+    del keys, vals, ko, vo
+
+    # more than 256 buckets (Section 6.3): two digit passes, n = 2^26 uniform keys
+    n = 1 << 26
+    keys_u = dev_u32(synthetic.uniform_u32(n, 51))
+    keys_f = dev_u32(synthetic.uniform_f32_1000(n, 52))
+    vals = dev_u32(synthetic.index_values(n))
+    ko, vo = torch.empty_like(vals), torch.empty_like(vals)
+    offs = torch.empty(65537, dtype=torch.int32, device=dev)
+    sptr = torch.cuda.current_stream().cuda_stream
+    for name, keys, spec in (("range_m1024", keys_u, ms.BucketSpec.range_u32(dev_u32(synthetic.range_splitters(1024, 53)))),
+                             ("range_m65536", keys_u, ms.BucketSpec.range_u32(dev_u32(synthetic.range_splitters(65536, 54)))),
+                             ("delta_f32_m65536", keys_f, ms.BucketSpec.delta_f32(65536, float(np.float32(1000.0) / np.float32(65536)))),
+                             ("mod_m65535", keys_u, ms.BucketSpec.mod(65535))):
+        cs = spec.c()
+        for pairs in (False, True):
+            def run_w():
+                if pairs:
+                    st = ms.ms_multisplit_pairs(keys.data_ptr(), vals.data_ptr(), n, cs, ko.data_ptr(),
+                                                vo.data_ptr(), offs.data_ptr(), sptr)
+                else:
+                    st = ms.ms_multisplit_keys(keys.data_ptr(), n, cs, ko.data_ptr(), offs.data_ptr(), sptr)
+                if st != ms.MS_OK:
+                    raise ms.MsError(st, name)
+
+            t = _time(torch, run_w, reps=5)
+            rate = metrics.rate_g(n, t * 1e-3)
+            comp = metrics.sol_rate_g(peak, metrics.compulsory_bytes_per_element(pairs))
+            out[f"wide_{name}_{'pairs' if pairs else 'keys'}"] = {
+                "ms": round(t, 4), ("gpairs_s" if pairs else "gkeys_s"): round(rate, 2),
+                "frac_compulsory_roofline": round(rate / comp, 4), "passes": 2}
+    del keys_u, keys_f, vals, ko, vo, offs
+    torch.cuda.empty_cache()
+
     # device histogram (Section 7.3): n = 2^26, Range (range splitters) and Even (float32 delta) buckets
     n = 1 << 26
     hk = dev_u32(synthetic.uniform_u32(n, 31))

@@ -59,7 +59,7 @@ typedef enum {
    * b <= 0 -> 0, b >= m (and +inf, NaN) -> m-1. */
   MS_BUCKET_DELTA_F32 = 1,
   /* radix digit (Section 7.1): (u >> shift) & (2^bits - 1); m must be 2^bits,
-   * 0 <= bits <= 8, shift + bits <= 32. */
+   * 0 <= bits <= 8 (<= 16 for ms_multisplit_keys / _pairs), shift + bits <= 32. */
   MS_BUCKET_RADIX = 2,
   /* u mod m. */
   MS_BUCKET_MOD = 3
@@ -67,13 +67,19 @@ typedef enum {
 
 typedef struct {
   int32_t kind;               /* an ms_bucket_kind */
-  uint32_t m;                 /* number of buckets, 1 <= m <= 256 */
+  uint32_t m;                 /* number of buckets, 1 <= m <= 256; up to 65536
+                               * for ms_multisplit_keys / ms_multisplit_pairs */
   const uint32_t *splitters;  /* RANGE_U32 only: device pointer, m-1 entries */
   float x0, delta;            /* DELTA_F32 only: delta > 0 and finite */
   uint32_t shift, bits;       /* RADIX only */
 } ms_bucket_spec;
 
 /* Stable multisplit of keys (Section 3.1, Eq. 1).
+ * With 257 <= m <= 65536 buckets (Section 6.3, larger multisplits) the call
+ * runs two multisplit passes over the 8-bit digits of the bucket id, least
+ * significant first, through a library pool buffer of n words (per array),
+ * then a bisection per bucket for the offsets; the result is the same stable
+ * multisplit, for every identifier kind.
  *   keys_in[n]   -> keys_out[n]: the keys grouped by bucket, buckets ascending,
  *                   input order kept inside each bucket.
  *   offsets[m+1] -> offsets[j] = start of bucket j in keys_out, offsets[m] = n
@@ -98,6 +104,14 @@ ms_status ms_multisplit_pairs(const uint32_t *keys_in, const uint32_t *vals_in, 
  * buffer of n words (per array) in its pool during the call. */
 ms_status ms_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, size_t n, int begin_bit,
                         int end_bit, uint32_t *keys_out, uint32_t *vals_out, void *stream);
+
+/* The same sort with r-bit digits, 1 <= r <= 8 (Section 6.3, the radix-width
+ * study of the sort table): ceil((end_bit - begin_bit) / r) multisplit passes
+ * into 2^r buckets, the last pass taking the bits left over (r = 7 on 32 bits:
+ * four 7-bit passes and one 4-bit pass).  Arguments and errors as for
+ * ms_radix_sort; MS_ERR_INVALID_ARG for r outside 1..8. */
+ms_status ms_radix_sort_r(const uint32_t *keys_in, const uint32_t *vals_in, size_t n, int begin_bit,
+                          int end_bit, int r, uint32_t *keys_out, uint32_t *vals_out, void *stream);
 
 /* Device histogram (Section 7.3, "Even" and "Range" histograms built on the
  * multisplit's pre-scan): counts[b] = number of keys whose bucket is b, for

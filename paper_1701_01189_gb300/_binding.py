@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_PKG, "_build", "libms.so")
 
 MS_OK, MS_ERR_INVALID_ARG, MS_ERR_UNSUPPORTED, MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA, MS_ERR_TIMEOUT = range(6)
 RANGE_U32, DELTA_F32, RADIX, MOD = 0, 1, 2, 3
-MAX_M = 256
+MAX_M = 256          # histogram, batched plans, the no-allocation entry point
+MAX_M_WIDE = 65536   # ms_multisplit_keys / ms_multisplit_pairs (two digit passes above MAX_M)
 
 
 class MsError(RuntimeError):
@@ -76,6 +77,7 @@ def lib() -> ctypes.CDLL:
         L.ms_multisplit_pairs.argtypes = [P, P, S, SP, P, P, P, P]
         L.ms_multisplit_keys_noalloc.argtypes = [P, S, SP, P, P, P]
         L.ms_radix_sort.argtypes = [P, P, S, I, I, P, P, P]
+        L.ms_radix_sort_r.argtypes = [P, P, S, I, I, I, P, P, P]
         L.ms_histogram.argtypes = [P, S, SP, P, P]
         L.ms_device_status.argtypes = [P]
         L.ms_status_string.argtypes = [I]
@@ -106,7 +108,7 @@ def lib() -> ctypes.CDLL:
         L.ms_stage_timing.argtypes = [I]
         L.ms_stage_times.argtypes = [P, P, P, P]
         for f in ("ms_multisplit_keys", "ms_multisplit_pairs", "ms_multisplit_keys_noalloc", "ms_radix_sort",
-                  "ms_histogram", "ms_device_status",
+                  "ms_radix_sort_r", "ms_histogram", "ms_device_status",
                   "ms_stage_timing", "ms_stage_times"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -131,6 +133,11 @@ def ms_multisplit_keys_noalloc(keys_in: int, n: int, spec: "_Spec", keys_out: in
 def ms_radix_sort(keys_in: int, vals_in: int, n: int, begin_bit: int, end_bit: int, keys_out: int,
                   vals_out: int, stream: int) -> int:
     return lib().ms_radix_sort(keys_in, vals_in, n, begin_bit, end_bit, keys_out, vals_out, stream)
+
+
+def ms_radix_sort_r(keys_in: int, vals_in: int, n: int, begin_bit: int, end_bit: int, r: int, keys_out: int,
+                    vals_out: int, stream: int) -> int:
+    return lib().ms_radix_sort_r(keys_in, vals_in, n, begin_bit, end_bit, r, keys_out, vals_out, stream)
 
 
 def ms_histogram(keys: int, n: int, spec: "_Spec", counts: int, stream: int) -> int:
@@ -344,8 +351,11 @@ def multisplit_pairs(keys, vals, spec: BucketSpec, keys_out=None, vals_out=None,
 
 
 def radix_sort(keys, vals=None, begin_bit: int = 0, end_bit: int = 32, keys_out=None, vals_out=None,
-               stream=None):
-    """LSD multisplit radix sort (Section 7.1).  Returns (keys_out, vals_out or None)."""
+               stream=None, r: Optional[int] = None):
+    """LSD multisplit radix sort (Section 7.1).  Returns (keys_out, vals_out or None).
+
+    ``r`` (1..8) sorts in r-bit digits (ms_radix_sort_r); None takes the tuned
+    method with 8-bit digits (ms_radix_sort)."""
     import torch
 
     keys = _u32_view(keys)
@@ -356,8 +366,12 @@ def radix_sort(keys, vals=None, begin_bit: int = 0, end_bit: int = 32, keys_out=
         vals = _u32_view(vals)
         vals_out = torch.empty_like(vals) if vals_out is None else vals_out
         vptr, voptr = vals.data_ptr(), vals_out.data_ptr()
-    _check(ms_radix_sort(keys.data_ptr(), vptr, n, begin_bit, end_bit, keys_out.data_ptr(), voptr,
-                         _stream(stream)), "ms_radix_sort")
+    if r is None:
+        _check(ms_radix_sort(keys.data_ptr(), vptr, n, begin_bit, end_bit, keys_out.data_ptr(), voptr,
+                             _stream(stream)), "ms_radix_sort")
+    else:
+        _check(ms_radix_sort_r(keys.data_ptr(), vptr, n, begin_bit, end_bit, int(r), keys_out.data_ptr(), voptr,
+                               _stream(stream)), "ms_radix_sort_r")
     return keys_out, (vals_out if vals is not None else None)
 
 

@@ -168,8 +168,12 @@ static ms_status multisplit_impl(const uint32_t* keys_in, const uint32_t* vals_i
                                  uint32_t* offsets, void* stream, bool pairs) {
   Call c;
   std::memset(&c, 0, sizeof c);
-  ms_status st = make_devspec(spec, &c.sp, &c.kind);
+  WideSpec w;
+  std::memset(&w, 0, sizeof w);
+  const bool wide = spec != nullptr && spec->m > (uint32_t)kMaxM;
+  ms_status st = wide ? make_wide_spec(spec, &w) : make_devspec(spec, &c.sp, &c.kind);
   if (st != MS_OK) return st;
+  const uint32_t m = wide ? w.fm : c.sp.m;
   if (n >= ((size_t)1 << 32)) return MS_ERR_INVALID_ARG;
   const size_t bytes = n * sizeof(uint32_t);
   if (n > 0) {
@@ -187,7 +191,7 @@ static ms_status multisplit_impl(const uint32_t* keys_in, const uint32_t* vals_i
   if (st != MS_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n == 0) {
-    if (offsets != nullptr) return to_status(cudaMemsetAsync(offsets, 0, (size_t)(c.sp.m + 1) * 4, s));
+    if (offsets != nullptr) return to_status(cudaMemsetAsync(offsets, 0, (size_t)(m + 1) * 4, s));
     return MS_OK;
   }
   c.keys_in = keys_in;
@@ -197,7 +201,7 @@ static ms_status multisplit_impl(const uint32_t* keys_in, const uint32_t* vals_i
   c.offsets = offsets;
   c.n = (uint32_t)n;
   c.stream = s;
-  return to_status(run_multisplit(c, *ctx));
+  return to_status(wide ? run_wide(c, w, *ctx) : run_multisplit(c, *ctx));
 }
 
 }  // namespace ms
@@ -237,12 +241,64 @@ extern "C" ms_status ms_histogram(const uint32_t* keys, size_t n, const ms_bucke
 }
 
 // Section 7.1: LSD passes of multisplit with the radix-digit identifier
-// f_k(u) = (u >> (begin + 8k)) & (2^r - 1), r = 8 except for a shorter last
+// f_k(u) = (u >> (begin + rk)) & (2^r - 1), r bits except for a shorter last
 // digit.  Each pass is a stable multisplit, so the composition is the stable
 // sort by bits [begin_bit, end_bit).  Buffers ping-pong between keys_out and a
 // pool buffer so that the last pass lands in keys_out.
-extern "C" ms_status ms_radix_sort(const uint32_t* keys_in, const uint32_t* vals_in, size_t n, int begin_bit,
-                                   int end_bit, uint32_t* keys_out, uint32_t* vals_out, void* stream) {
+static cudaError_t sort_by_multisplit_passes(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t n,
+                                             int begin_bit, int end_bit, int r, uint32_t* keys_out,
+                                             uint32_t* vals_out, cudaStream_t s, DeviceCtx& ctx) {
+  const bool pairs = vals_in != nullptr;
+  const size_t bytes = (size_t)n * sizeof(uint32_t);
+  const int width = end_bit - begin_bit;
+  const int passes = (width + r - 1) / r;
+  void* tmp = nullptr;
+  uint32_t* tmp_k = nullptr;
+  uint32_t* tmp_v = nullptr;
+  if (passes > 1) {
+    const size_t arr = (bytes + 255) & ~(size_t)255;  // keeps the value array 256-byte aligned
+    cudaError_t e = scratch_alloc(ctx, &tmp, arr * (pairs ? 2 : 1), s);
+    if (e != cudaSuccess) return e;
+    tmp_k = static_cast<uint32_t*>(tmp);
+    tmp_v = pairs ? reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + arr) : nullptr;
+  }
+  const uint32_t* src_k = keys_in;
+  const uint32_t* src_v = vals_in;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < passes && e == cudaSuccess; ++p) {
+    const int shift = begin_bit + r * p;
+    const int bits = (end_bit - shift) < r ? (end_bit - shift) : r;
+    const bool to_out = ((passes - 1 - p) % 2) == 0;
+    uint32_t* dst_k = to_out ? keys_out : tmp_k;
+    uint32_t* dst_v = to_out ? vals_out : tmp_v;
+    Call c;
+    std::memset(&c, 0, sizeof c);
+    c.kind = kRadix;
+    c.sp.m = 1u << bits;
+    c.sp.nbits = (uint32_t)bits;
+    c.sp.m_pad = c.sp.m <= 32 ? 32u : c.sp.m;
+    c.sp.lut_bits = 10u;
+    c.sp.shift = (uint32_t)shift;
+    c.sp.mask = (1u << bits) - 1u;
+    c.keys_in = src_k;
+    c.vals_in = pairs ? src_v : nullptr;
+    c.keys_out = dst_k;
+    c.vals_out = pairs ? dst_v : nullptr;
+    c.offsets = nullptr;
+    c.n = n;
+    c.stream = s;
+    e = run_multisplit(c, ctx);
+    src_k = dst_k;
+    src_v = dst_v;
+  }
+  const cudaError_t e2 = scratch_free(tmp, s);
+  return e != cudaSuccess ? e : e2;
+}
+
+// Shared argument handling of the two sorts; r = 0 picks the tuned method
+// with 8-bit digits.
+static ms_status radix_sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, size_t n, int begin_bit,
+                                 int end_bit, int r, uint32_t* keys_out, uint32_t* vals_out, void* stream) {
   if (begin_bit < 0 || end_bit > 32 || begin_bit > end_bit) return MS_ERR_INVALID_ARG;
   if (n >= ((size_t)1 << 32)) return MS_ERR_INVALID_ARG;
   const bool pairs = vals_in != nullptr || vals_out != nullptr;
@@ -265,52 +321,26 @@ extern "C" ms_status ms_radix_sort(const uint32_t* keys_in, const uint32_t* vals
     if (e == cudaSuccess && pairs) e = cudaMemcpyAsync(vals_out, vals_in, bytes, cudaMemcpyDeviceToDevice, s);
     return to_status(e);
   }
-  if (n < ((size_t)1 << 30) && choose_sort_method((uint32_t)n, pairs) == 0)
+  if (r == 0 && n < ((size_t)1 << 30) && choose_sort_method((uint32_t)n, pairs) == 0)
     return to_status(run_onesweep_sort(keys_in, pairs ? vals_in : nullptr, (uint32_t)n, begin_bit, end_bit, keys_out,
                                        pairs ? vals_out : nullptr, s, *ctx));
-  // one three-stage multisplit per digit (tuned, or n >= 2^30, beyond the
-  // one-sweep kernels' 30-bit status counts)
-  const int passes = (width + 7) / 8;
-  void* tmp = nullptr;
-  uint32_t* tmp_k = nullptr;
-  uint32_t* tmp_v = nullptr;
-  if (passes > 1) {
-    cudaError_t e = scratch_alloc(*ctx, &tmp, bytes * (pairs ? 2 : 1), s);
-    if (e != cudaSuccess) return to_status(e);
-    tmp_k = static_cast<uint32_t*>(tmp);
-    tmp_v = pairs ? tmp_k + n : nullptr;
-  }
-  const uint32_t* src_k = keys_in;
-  const uint32_t* src_v = vals_in;
-  cudaError_t e = cudaSuccess;
-  for (int p = 0; p < passes && e == cudaSuccess; ++p) {
-    const int shift = begin_bit + 8 * p;
-    const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
-    const bool to_out = ((passes - 1 - p) % 2) == 0;
-    uint32_t* dst_k = to_out ? keys_out : tmp_k;
-    uint32_t* dst_v = to_out ? vals_out : tmp_v;
-    Call c;
-    std::memset(&c, 0, sizeof c);
-    c.kind = kRadix;
-    c.sp.m = 1u << bits;
-    c.sp.nbits = (uint32_t)bits;
-    c.sp.m_pad = c.sp.m <= 32 ? 32u : c.sp.m;
-    c.sp.lut_bits = 10u;
-    c.sp.shift = (uint32_t)shift;
-    c.sp.mask = (1u << bits) - 1u;
-    c.keys_in = src_k;
-    c.vals_in = pairs ? src_v : nullptr;
-    c.keys_out = dst_k;
-    c.vals_out = pairs ? dst_v : nullptr;
-    c.offsets = nullptr;
-    c.n = (uint32_t)n;
-    c.stream = s;
-    e = run_multisplit(c, *ctx);
-    src_k = dst_k;
-    src_v = dst_v;
-  }
-  const cudaError_t e2 = scratch_free(tmp, s);
-  return to_status(e != cudaSuccess ? e : e2);
+  // one three-stage multisplit per digit (tuned; other digit widths; or
+  // n >= 2^30, beyond the one-sweep kernels' 30-bit status counts)
+  return to_status(sort_by_multisplit_passes(keys_in, pairs ? vals_in : nullptr, (uint32_t)n, begin_bit, end_bit,
+                                             r == 0 ? 8 : r, keys_out, pairs ? vals_out : nullptr, s, *ctx));
+}
+
+extern "C" ms_status ms_radix_sort(const uint32_t* keys_in, const uint32_t* vals_in, size_t n, int begin_bit,
+                                   int end_bit, uint32_t* keys_out, uint32_t* vals_out, void* stream) {
+  return radix_sort_impl(keys_in, vals_in, n, begin_bit, end_bit, 0, keys_out, vals_out, stream);
+}
+
+// Section 6.3 / Table 8: the same sort with r-bit digits (1 <= r <= 8), each
+// pass a multisplit into 2^r buckets.
+extern "C" ms_status ms_radix_sort_r(const uint32_t* keys_in, const uint32_t* vals_in, size_t n, int begin_bit,
+                                     int end_bit, int r, uint32_t* keys_out, uint32_t* vals_out, void* stream) {
+  if (r < 1 || r > 8) return MS_ERR_INVALID_ARG;
+  return radix_sort_impl(keys_in, vals_in, n, begin_bit, end_bit, r, keys_out, vals_out, stream);
 }
 
 extern "C" ms_status ms_test_expire_lookback(void* stream) {

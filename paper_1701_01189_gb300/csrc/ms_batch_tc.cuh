@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
   uint32_t* s_tbl = smem + Lay::tbl(R);
   uint32_t* s_lut = smem + Lay::lut(R);
   const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
-  const TcLut L{s_lut, 32u - lb, lw, lane & ((1u << lw) - 1u), (1u << (32u - lb)) - 1u};
+  const TcLut L{s_lut, 32u - lb, lw, lane & ((1u << lw) - 1u), (1u << (32u - lb)) - 1u, s_tbl};
   uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)
 
   for (uint32_t i = t; i < R * kTcRow; i += kTcThreads) s_cnt[i] = 0u;

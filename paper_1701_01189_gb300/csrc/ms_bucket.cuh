@@ -31,11 +31,57 @@ __device__ __forceinline__ uint32_t range_search(uint32_t u, const uint32_t* tbl
   return min(pos, m - 1);
 }
 
+// Table of the super-bucket splitters of a wide range identifier: entry i is
+// s_{256(i+1)}, the first splitter of super-bucket i+1 (mc - 1 of them),
+// padded with 0xffffffff to 2^NB - 1 entries.  The count of these <= u is
+// floor(f(u) / 256): with nondecreasing splitters, f(u) >= 256 j exactly when
+// s_{256 j} <= u.  No barrier.
+template <int NB>
+__device__ __forceinline__ void build_wide_table(const DevSpec& sp, uint32_t* tbl) {
+  constexpr uint32_t P = (1u << NB) - 1u;
+  if (sp.base == kRange)
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+      tbl[i] = (i + 1u < sp.mc) ? sp.splitters[256u * (i + 1u) - 1u] : 0xffffffffu;
+}
+
+// f(u) of a wide identifier (fm > 256 buckets) and then its digit
+// (f(u) >> dshift) & dmask.  Range: the super-bucket S from the table of
+// build_wide_table, then a bisection over the at most 255 splitters inside S
+// (s_{256S+1} ..), read through the read-only cache.  Delta and mod as for
+// 256 buckets or fewer, with fm buckets.
+template <int NB>
+__device__ __forceinline__ uint32_t wide_bucket(uint32_t u, const DevSpec& sp, const uint32_t* tbl) {
+  uint32_t b;
+  if (sp.base == kRange) {
+    uint32_t S = 0;
+    if constexpr (NB > 0) S = range_search<NB>(u, tbl, sp.mc);
+    const uint32_t* blk = sp.splitters + 256u * S;
+    const uint32_t cnt = min(255u, sp.fm - 1u - 256u * S);
+    uint32_t pos = 0;
+#pragma unroll
+    for (int s = 7; s >= 0; --s) {
+      const uint32_t h = 1u << s, i = pos + h - 1u;
+      pos += (i < cnt && __ldg(blk + i) <= u) ? h : 0u;
+    }
+    b = 256u * S + pos;
+  } else if (sp.base == kDelta) {
+    const float x = __uint_as_float(u);
+    const float f = floorf(__fdiv_rn(__fsub_rn(x, sp.x0), sp.delta));
+    b = !(f < (float)sp.fm) ? sp.fm - 1u : (f <= 0.0f ? 0u : (uint32_t)f);
+  } else {
+    const uint32_t t = __umulhi(sp.mod_magic, u);
+    const uint32_t q = (t + ((u - t) >> sp.mod_sh1)) >> sp.mod_sh2;
+    b = u - q * sp.fm;
+  }
+  return (b >> sp.dshift) & sp.dmask;
+}
+
 // Builds the splitter table (2^NB - 1 words) and, for range buckets, the
 // lookup table of 2^lb cells (uint2 each).  All threads of the block call it;
 // ends with a block barrier.
 template <int KIND, int NB>
 __device__ __forceinline__ void build_bucket_tables(const DevSpec& sp, uint32_t* tbl, uint2* lut) {
+  if constexpr (KIND == kWide) build_wide_table<NB>(sp, tbl);
   if constexpr (KIND == kRange) {
     const uint32_t P = 1u << NB;
     for (uint32_t i = threadIdx.x; i + 1 < P; i += blockDim.x)
@@ -88,6 +134,8 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t u, const DevSpec& sp, con
     return (uint32_t)f;
   } else if constexpr (KIND == kRadix) {
     return (u >> sp.shift) & sp.mask;
+  } else if constexpr (KIND == kWide) {
+    return wide_bucket<NB>(u, sp, tbl);
   } else {
     // u mod m by the multiply-shift division of Granlund and Montgomery
     // ("Division by invariant integers using multiplication", PLDI 1994,

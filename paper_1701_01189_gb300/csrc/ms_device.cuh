@@ -19,12 +19,17 @@ namespace ms {
 
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kMaxM = 256;
+// Identifiers with more buckets (up to 2^16) run as two passes over the
+// digits of the bucket id (kWide).
+constexpr uint32_t kMaxWideM = 65536;
 
 // Bits of the per-device status word.
 constexpr uint32_t kDevErrTimeout = 1u;  // a bounded wait expired
 constexpr uint32_t kDevErrBounds = 2u;   // an index failed its bounds check (the access was skipped)
 
-enum Kind : int { kRange = 0, kDelta = 1, kRadix = 2, kMod = 3 };
+// kWide: one 8-bit digit of the bucket id of an identifier with more than 256
+// buckets (its kind in DevSpec::base), least significant digit first.
+enum Kind : int { kRange = 0, kDelta = 1, kRadix = 2, kMod = 3, kWide = 4 };
 
 // How the post-scan ranks keys: ballot voting or peer tables inside each
 // warp, per-thread bucket counters (m <= 32; ms_tc.cuh), or peers found by
@@ -42,6 +47,10 @@ struct DevSpec {
   uint32_t mod_magic, mod_sh1, mod_sh2;  // kMod: multiply-shift constants
   uint32_t m_pad;             // m rounded up to a multiple of 32 (at least 32)
   uint32_t lut_bits;          // kRange: key bits indexing the splitter lookup table
+  // kWide only: the identifier is `base` (kRange, kDelta or kMod) with fm
+  // buckets (257 .. 2^16; for kRange fm-1 splitters and mc = ceil(fm / 256)
+  // super-buckets), and the kernel's bucket is (f(u) >> dshift) & dmask.
+  uint32_t base, fm, mc, dshift, dmask;
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

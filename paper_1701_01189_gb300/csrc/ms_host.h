@@ -78,6 +78,20 @@ bool overlap(const void* a, const void* b, size_t bytes);
 // The calling device's state, created on first use (allocates: not inside a capture).
 ms_status current_device_ctx(DeviceCtx** out);
 
+// An identifier with 257 .. 2^16 buckets (ms_wide.cu): the kernel kind of its
+// digit passes (kWide, or kRadix for a radix digit of 9..16 bits), its bucket
+// count fm, its super-bucket count mc = ceil(fm / 256), and the kernel spec of
+// the whole bucket id (dshift 0, every bit kept).
+struct WideSpec {
+  int kind;
+  uint32_t fm, mc;
+  DevSpec full;
+};
+ms_status make_wide_spec(const ms_bucket_spec* spec, WideSpec* out);
+// Stable multisplit by a wide identifier: two digit passes through a pool
+// buffer, then the bucket offsets (c.offsets, fm + 1 entries, if not null).
+cudaError_t run_wide(const Call& c, const WideSpec& w, DeviceCtx& ctx);
+
 // LSD radix sort with one sweep per digit (ms_onesweep.cu); n < 2^30.
 cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t n, int begin_bit, int end_bit,
                               uint32_t* keys_out, uint32_t* vals_out, cudaStream_t s, DeviceCtx& ctx);

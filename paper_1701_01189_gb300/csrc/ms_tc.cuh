@@ -131,6 +131,7 @@ __host__ __device__ constexpr uint32_t tc_lut_words(int kind, uint32_t lb, uint3
 template <int KIND, int BB = 5>
 __device__ __forceinline__ void tc_build_tables(const DevSpec& sp, uint32_t lb, uint32_t lw, uint32_t* tbl,
                                                 uint32_t* lut) {
+  if constexpr (KIND == kWide) build_wide_table<BB>(sp, tbl);
   if constexpr (KIND == kRange) {
     constexpr uint32_t P = (1u << BB) - 1u;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) tbl[i] = (i + 1 < sp.m) ? sp.splitters[i] : 0xffffffffu;
@@ -163,6 +164,7 @@ struct TcLut {
   uint32_t lw;    // log2 of the copies
   uint32_t rep;   // this lane's copy
   uint32_t fmask; // 2^sh - 1
+  const uint32_t* tbl;  // splitter table (kWide: super-bucket splitters)
   __device__ __forceinline__ uint32_t word(uint32_t u) const { return lut[((u >> sh) << lw) + rep]; }
 };
 
@@ -172,6 +174,8 @@ __device__ __forceinline__ uint32_t tc_bucket(uint32_t u, const DevSpec& sp, con
     const uint32_t e = L.word(u);
     flag |= e;
     return (e & ((1u << BB) - 1u)) + ((u & L.fmask) >= (e >> (BB + 1)) ? 1u : 0u);
+  } else if constexpr (KIND == kWide) {
+    return wide_bucket<BB>(u, sp, L.tbl);
   } else {
     return bucket_of<KIND, BB>(u, sp, nullptr, nullptr);
   }
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
   uint32_t* s_tbl = smem + cnt_words;
   uint32_t* s_lut = s_tbl + (MODE == kCountLaneBytes ? 256u : 32u);
   const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
-  const TcLut L{s_lut, 32u - a.lb, a.lw, lane & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u};
+  const TcLut L{s_lut, 32u - a.lb, a.lw, lane & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u, s_tbl};
 
   for (uint32_t i = t; i < cnt_words; i += kTcThreads) s_cnt[i] = 0u;
   tc_build_tables<KIND, BB>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
   uint32_t* s_lut = base + Lay::lut(R);
 
   const uint32_t t = threadIdx.x;
-  const TcLut L{s_lut, 32u - a.lb, a.lw, t & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u};
+  const TcLut L{s_lut, 32u - a.lb, a.lw, t & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u, s_tbl};
   const uint32_t c = blockIdx.x;
   const uint32_t t0 = c * a.tiles_per_cta;
   const uint32_t t1 = min(t0 + a.tiles_per_cta, a.num_tiles);

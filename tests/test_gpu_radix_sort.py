@@ -132,3 +132,24 @@ def test_sort_by_multisplit_passes(bits, n):
         np.testing.assert_array_equal(gk2, ek)
     finally:
         ms.ms_tune_reset()
+
+
+@pytest.mark.parametrize("r", [1, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("bits", [(0, 32), (3, 30), (0, 16)])
+@pytest.mark.parametrize("n", [1, 4097, (1 << 20) + 5])
+def test_sort_with_r_bit_digits(r, bits, n):
+    """The sort in r-bit digits (ceil(width / r) passes, the last one taking the
+    bits left over), keys and pairs, against the oracle."""
+    import paper_1701_01189_gb300 as ms
+    import torch
+
+    keys = synthetic.uniform_u32(n, 17 * r + n)
+    vals = synthetic.index_values(n)
+    ek, ev = oracle.radix_sort(keys, vals, *bits)
+    ko, vo = ms.radix_sort(to_dev(keys), to_dev(vals), *bits, r=r)
+    ko2, _ = ms.radix_sort(to_dev(keys), None, *bits, r=r)
+    torch.cuda.synchronize()
+    assert ms.device_status() == ms.MS_OK
+    np.testing.assert_array_equal(to_host(ko), ek)
+    np.testing.assert_array_equal(to_host(vo), ev)
+    np.testing.assert_array_equal(to_host(ko2), ek)

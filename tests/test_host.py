@@ -58,7 +58,14 @@ def _spec(kind, m, **kw):
 
 BAD_SPECS = [
     _spec(ms.MOD, 0),
-    _spec(ms.MOD, 257),
+    _spec(ms.MOD, 65537),
+    _spec(ms.RANGE_U32, 70000, splitters=0x5000),
+    _spec(ms.RANGE_U32, 300, splitters=None),
+    _spec(ms.DELTA_F32, 1000, delta=0.0),
+    _spec(ms.RADIX, 1 << 17, shift=0, bits=17),
+    _spec(ms.RADIX, 1 << 16, shift=20, bits=16),
+    _spec(ms.RADIX, 1000, shift=0, bits=10),
+    _spec(9, 1000),
     _spec(ms.RANGE_U32, 4, splitters=None),
     _spec(ms.DELTA_F32, 8, delta=0.0),
     _spec(ms.DELTA_F32, 8, delta=-1.0),
@@ -66,14 +73,42 @@ BAD_SPECS = [
     _spec(ms.DELTA_F32, 8, delta=1.0, x0=float("nan")),
     _spec(ms.RADIX, 256, shift=28, bits=8),
     _spec(ms.RADIX, 128, shift=0, bits=8),
-    _spec(ms.RADIX, 512, shift=0, bits=9),
+    _spec(ms.RADIX, 512, shift=0, bits=8),
     _spec(7, 8),
+]
+
+# valid for ms_multisplit_keys / _pairs (two digit passes) but not for the
+# histogram, batched plans and the no-allocation entry point (m <= 256)
+WIDE_SPECS = [
+    _spec(ms.MOD, 257),
+    _spec(ms.DELTA_F32, 65536, delta=1.0),
+    _spec(ms.RANGE_U32, 1000, splitters=0x5000),
+    _spec(ms.RADIX, 512, shift=0, bits=9),
 ]
 
 
 @pytest.mark.parametrize("i", range(len(BAD_SPECS)))
 def test_bad_spec_rejected_before_device(lib, i):
     assert ms.ms_multisplit_keys(0x1000, 16, BAD_SPECS[i], 0x2000, 0, None) == ms.MS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("i", range(len(WIDE_SPECS)))
+def test_wide_specs_only_for_the_plain_calls(lib, i):
+    spec = WIDE_SPECS[i]
+    assert ms.ms_histogram(0x1000, 16, spec, 0x2000, None) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_multisplit_keys_noalloc(0x1000, 16, spec, 0x2000, 0, None) == ms.MS_ERR_INVALID_ARG
+    st, _h = ms.ms_batch_plan_create([(0x1000, None, 0x2000, None, 0x3000, 16)], spec)
+    assert st == ms.MS_ERR_INVALID_ARG
+    # the plain call checks the pointers first (no device work here)
+    assert ms.ms_multisplit_keys(None, 16, spec, 0x2000, 0, None) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_multisplit_keys(0x1000, 16, spec, 0x1020, 0, None) == ms.MS_ERR_INVALID_ARG
+
+
+def test_bad_radix_width_rejected(lib):
+    for r in (0, 9, -1):
+        assert ms.ms_radix_sort_r(0x1000, None, 16, 0, 32, r, 0x2000, None, None) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_radix_sort_r(0x1000, None, 16, 8, 4, 4, 0x2000, None, None) == ms.MS_ERR_INVALID_ARG
+    assert ms.ms_radix_sort_r(0x1000, None, 16, 0, 32, 4, 0x1000, None, None) == ms.MS_ERR_INVALID_ARG
 
 
 def test_bad_pointers_rejected(lib):

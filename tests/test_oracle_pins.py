@@ -146,9 +146,10 @@ def pin_bruteforce_exhaustive(mutant=0):
 
 def pin_random_vs_argsort(mutant=0):
     g = synthetic.rng(5)
-    for trial in range(24):
+    for trial in range(36):
         n = int(g.integers(0, 4097))
-        m = int(g.choice([1, 2, 3, 8, 31, 32, 33, 64, 255, 256]))
+        # m beyond 256 too: Eq. 1 defines the result for any bucket count (Section 6.3)
+        m = int(g.choice([1, 2, 3, 8, 31, 32, 33, 64, 255, 256, 257, 1000, 65536]))
         keys = synthetic.uniform_u32(n, 100 + trial)
         kind = trial % 3
         if kind == 0:
