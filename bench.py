@@ -139,10 +139,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_sources(names):
+    """The files that define the sweep's kernels: the device headers and the
+    per-identifier translation units that instantiate them."""
+    return sorted(n for n in names if n.endswith(".cuh") or (n.startswith("ms_kind_") and n.endswith(".cu")))
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1701_01189_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in kernel_sources(os.listdir(csrc)):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())

@@ -2,8 +2,8 @@
 // for larger multisplits").
 //
 // The paper iterates multisplit over super-buckets of at most 256 buckets,
-// most significant group first, and notes that this needs an identifier
-// whose nearby keys land in nearby buckets.  Here the iteration runs over the
+// most significant group first, which restricts it to identifiers whose
+// adjacent bucket ids cover adjacent key ranges.  Here the iteration runs over the
 // 8-bit digits of the bucket id b = f(u), least significant digit first: pass
 // 0 is a stable multisplit by b mod 256, pass 1 a stable multisplit by
 // floor(b / 256).  Each pass is stable, so the pair of passes orders the
