@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArg
   const DevSpec& sp = a.sp;
   const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1, lb = sp.lut_bits;
   uint32_t* s_tbl = smem;
-  uint2* s_lut = reinterpret_cast<uint2*>(smem + Lay::lut());
+  uint32_t* s_lut = smem + Lay::lut();
   uint32_t* s_base = smem + Lay::base(lb);
   uint32_t* s_delta = s_base + 256;
   uint32_t* s_warp = s_delta + 256;

@@ -51,6 +51,8 @@ struct DevSpec {
   // buckets (257 .. 2^16; for kRange fm-1 splitters and mc = ceil(fm / 256)
   // super-buckets), and the kernel's bucket is (f(u) >> dshift) & dmask.
   uint32_t base, fm, mc, dshift, dmask;
+  const uint32_t* wlut;  // kWide range: global lookup table of 2^wlb cells (ms_bucket.cuh)
+  uint32_t wlb;
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

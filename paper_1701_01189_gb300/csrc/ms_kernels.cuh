@@ -100,7 +100,7 @@ __device__ __forceinline__ void prescan_flush(uint32_t* wwords, uint32_t* wtot, 
 // (ballot mode) the warp's count of bucket b.
 template <int KIND, int NB, int ITEMS, int RANK, bool FULL>
 __device__ __forceinline__ void rank_windows(const uint32_t* wk, uint32_t avail, const DevSpec& sp,
-                                             const uint32_t* s_tbl, const uint2* s_lut, uint32_t* wc,
+                                             const uint32_t* s_tbl, const uint32_t* s_lut, uint32_t* wc,
                                              uint32_t* wpeer, uint32_t m_pad, uint32_t m, const uint32_t* lane_x,
                                              uint32_t lt_mask, uint32_t lane, uint32_t (&rb)[ITEMS]) {
   if constexpr (RANK == kRankTable || RANK == kRankVote) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   uint32_t* ring_k = smem + Lay::kRing;
   uint32_t* ring_v = ring_k + STAGES * T;  // pairs
   uint32_t* s_tbl = smem + Lay::tbl();
-  uint2* s_lut = reinterpret_cast<uint2*>(smem + Lay::lut());
+  uint32_t* s_lut = smem + Lay::lut();
   uint32_t* s_run = smem + Lay::run(lb);
   uint32_t* s_delta = s_run + 256;
   uint32_t* s_warp = s_delta + 256;

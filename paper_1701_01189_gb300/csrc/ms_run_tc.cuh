@@ -81,8 +81,10 @@ static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking&
                                   uint32_t* arrive, uint32_t* offsets) {
   const uint32_t m = c.sp.m;
   const int mode = m <= 8 ? kCountReg : m <= 32 ? kCountThread : kCountLaneBytes;
-  // splitter lookup tables: 1024 cells x 8 copies (m <= 32), 2048 cells x 2 copies beyond
-  const uint32_t lb = mode == kCountLaneBytes ? 11u : 10u, lw = mode == kCountLaneBytes ? 1u : 3u;
+  // splitter lookup tables: 1024 cells x 8 copies (m <= 32), 4096 cells x 1 copy beyond
+  // (with random cells two copies barely thin the bank conflicts; twice the
+  // cells halve the flagged ones)
+  const uint32_t lb = mode == kCountLaneBytes ? 12u : 10u, lw = mode == kCountLaneBytes ? 0u : 3u;
   const bool vec = ((reinterpret_cast<uintptr_t>(c.keys_in)) & 15u) == 0;
   const size_t keep_tiles = kTcL2KeepBytes / ((size_t)kTcTile * 4);
   const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);

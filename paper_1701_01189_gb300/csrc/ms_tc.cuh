@@ -111,15 +111,8 @@ __device__ __forceinline__ uint32_t tc_block_scan(uint32_t v, uint32_t* s_warp, 
   return pre + x - v;
 }
 
-// Splitter lookup table of these kernels (range buckets): 2^lb cells of the
-// key space (its top lb bits), each one 32-bit word -- the bucket of the
-// cell's first key (bits 0..BB-1; BB = 5 for m <= 32, 8 for m <= 256), a flag
-// for a cell holding two or more splitters (bit BB), and the low 32 - lb bits
-// of the cell's single splitter (from bit BB+1; 2^(32-lb), above every key,
-// when it holds none) -- stored W = 2^lw times side by side: lane l reads copy
-// l mod W, so a warp's random lookups spread over W times as many banks.  A
-// flagged cell's keys take the full search over the splitter table
-// (tc_fixup).  Needs 32 - lb <= 30 - BB.
+// Splitter lookup table of these kernels (range buckets): the packed table of
+// build_packed_lut (ms_bucket.cuh) with BB = 5 for m <= 32 and 8 for m <= 256.
 constexpr uint32_t kTcLutFlag = 32u;  // the flag bit for BB = 5
 
 __host__ __device__ constexpr uint32_t tc_lut_words(int kind, uint32_t lb, uint32_t lw) {
@@ -136,28 +129,14 @@ __device__ __forceinline__ void tc_build_tables(const DevSpec& sp, uint32_t lb, 
     constexpr uint32_t P = (1u << BB) - 1u;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) tbl[i] = (i + 1 < sp.m) ? sp.splitters[i] : 0xffffffffu;
     __syncthreads();
-    const uint32_t sh = 32u - lb, fmask = (1u << sh) - 1u, W = 1u << lw, m = sp.m;
-    for (uint32_t cell = threadIdx.x; cell < (1u << lb); cell += blockDim.x) {
-      const uint32_t first = cell << sh, last = first | fmask;
-      // splitters <= x, clamped to m - 1, is the bucket of x
-      const uint32_t lo = min(first == 0u ? 0u : range_search<BB>(first - 1u, tbl, m + 1u), m - 1u);
-      const uint32_t hi = min(range_search<BB>(last, tbl, m + 1u), m - 1u);
-      uint32_t e;
-      if (hi == lo)
-        e = lo | ((fmask + 1u) << (BB + 1));
-      else if (hi == lo + 1u)
-        e = lo | ((tbl[lo] & fmask) << (BB + 1));
-      else
-        e = 1u << BB;
-      for (uint32_t r = 0; r < W; ++r) lut[(cell << lw) + r] = e;
-    }
+    build_packed_lut<BB>(sp, lb, lw, tbl, lut);
   }
   __syncthreads();
 }
 
 // Bucket of u by the fast path.  For range buckets the bucket returned for a
 // key of a flagged cell is wrong; callers OR the table words into `flag` and
-// redo the flagged keys with tc_fixup.
+// redo the flagged keys with tc_fixup (rare: the fast path stays lean).
 struct TcLut {
   const uint32_t* lut;
   uint32_t sh;    // 32 - lb
@@ -173,7 +152,7 @@ __device__ __forceinline__ uint32_t tc_bucket(uint32_t u, const DevSpec& sp, con
   if constexpr (KIND == kRange) {
     const uint32_t e = L.word(u);
     flag |= e;
-    return (e & ((1u << BB) - 1u)) + ((u & L.fmask) >= (e >> (BB + 1)) ? 1u : 0u);
+    return packed_fast<BB>(u, e, L.fmask);
   } else if constexpr (KIND == kWide) {
     return wide_bucket<BB>(u, sp, L.tbl);
   } else {
@@ -186,7 +165,13 @@ __device__ __forceinline__ void tc_fixup(const uint32_t (&key)[N], uint32_t (&bk
                                          const uint32_t* tbl, uint32_t m) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    if (L.word(key[i]) & (1u << BB)) bk[i] = range_search<BB>(key[i], tbl, m);
+    const uint32_t e = L.word(key[i]);
+    // m <= 32: five halving steps; m <= 256: the cell's few splitters
+    if constexpr (BB <= 5) {
+      if (e & (1u << BB)) bk[i] = range_search<BB>(key[i], tbl, m);
+    } else {
+      if (e & (1u << BB)) bk[i] = range_in_cell<BB>(key[i], e, tbl, m);
+    }
   }
 }
 
@@ -336,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
       const uint32_t u = a.keys[tb + p];
       uint32_t b = tc_bucket<KIND, BB>(u, sp, L, flag);
       if constexpr (KIND == kRange)
-        if (flag & (1u << BB)) b = range_search<BB>(u, s_tbl, m);
+        if (flag & (1u << BB)) b = range_in_cell<BB>(u, L.word(u), s_tbl, m);
       count1(b);
     }
     since += 16u;

@@ -64,6 +64,41 @@ __global__ void __launch_bounds__(256) k_wide_offsets(const uint32_t* out, uint3
   offsets[j] = lo;
 }
 
+// Number of the fm - 1 splitters <= x (bisection in global memory).
+__device__ __forceinline__ uint32_t count_le(const uint32_t* s, uint32_t cnt, uint32_t x) {
+  uint32_t lo = 0, hi = cnt;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(s + mid) <= x)
+      lo = mid + 1u;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// The global lookup table of a wide range identifier (layout beside
+// kWideLutFlag in ms_bucket.cuh): cell c covers keys [c << (32 - wlb),
+// ((c + 1) << (32 - wlb)) - 1]; lo = splitters below its first key, hi =
+// splitters up to its last key; the keys of the cell have buckets lo .. hi.
+__global__ void __launch_bounds__(256) k_wide_lut(const uint32_t* splitters, uint32_t fm, uint32_t wlb,
+                                                  uint32_t* lut) {
+  const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= (1u << wlb)) return;
+  const uint32_t sh = 32u - wlb, fmask = (1u << sh) - 1u;
+  const uint32_t first = cell << sh, last = first | fmask;
+  const uint32_t lo = first == 0u ? 0u : count_le(splitters, fm - 1u, first - 1u);
+  const uint32_t hi = count_le(splitters, fm - 1u, last);
+  uint32_t e;
+  if (hi == lo)
+    e = lo | ((fmask + 1u) << 17);
+  else if (hi == lo + 1u)
+    e = lo | ((__ldg(splitters + lo) & fmask) << 17);
+  else
+    e = lo | kWideLutFlag | (min(hi - lo, 255u) << 17);
+  lut[cell] = e;
+}
+
 static uint32_t log2_ceil(uint32_t m) {
   uint32_t l = 0;
   while ((1u << l) < m) ++l;
@@ -141,7 +176,11 @@ cudaError_t run_wide(const Call& c, const WideSpec& w, DeviceCtx& ctx) {
   const bool pairs = c.vals_in != nullptr;
   const size_t arr = (((size_t)c.n * 4) + 255) & ~(size_t)255;  // 256-byte aligned arrays
   const size_t coff_bytes = (((size_t)w.mc + 1) * 4 + 15) & ~(size_t)15;
-  const size_t bytes = arr * (pairs ? 2 : 1) + coff_bytes + (size_t)w.mc * 4;
+  // range: a cell per 16 buckets or more (few cells hold two splitters), 2^18 .. 2^20 cells
+  const uint32_t wlb = std::min(20u, std::max(18u, log2_ceil(w.fm) + 4u));
+  const size_t lut_bytes = w.full.base == kRange && w.kind == kWide ? ((size_t)4 << wlb) : 0;
+  const size_t mc_bytes = ((size_t)w.mc * 4 + 15) & ~(size_t)15;
+  const size_t bytes = arr * (pairs ? 2 : 1) + coff_bytes + mc_bytes + lut_bytes;
   void* ws = nullptr;
   cudaError_t e = scratch_alloc(ctx, &ws, bytes, c.stream);
   if (e != cudaSuccess) return e;
@@ -150,6 +189,14 @@ cudaError_t run_wide(const Call& c, const WideSpec& w, DeviceCtx& ctx) {
   uint32_t* tmp_v = pairs ? reinterpret_cast<uint32_t*>(base + arr) : nullptr;
   uint32_t* coff = reinterpret_cast<uint32_t*>(base + arr * (pairs ? 2 : 1));
   uint32_t* coarse = reinterpret_cast<uint32_t*>(base + arr * (pairs ? 2 : 1) + coff_bytes);
+  uint32_t* wlut = reinterpret_cast<uint32_t*>(base + arr * (pairs ? 2 : 1) + coff_bytes + mc_bytes);
+  WideSpec wf = w;  // the full spec with the lookup table in place (range)
+  if (lut_bytes) {
+    wf.full.wlut = wlut;
+    wf.full.wlb = wlb;
+    k_wide_lut<<<(1u << wlb) / 256u, 256, 0, c.stream>>>(w.full.splitters, w.fm, wlb, wlut);
+    e = cudaGetLastError();
+  }
 
   Call p0 = c, p1 = c;
   p0.keys_out = tmp_k;
@@ -168,18 +215,19 @@ cudaError_t run_wide(const Call& c, const WideSpec& w, DeviceCtx& ctx) {
       return cudaErrorInvalidValue;
     }
   } else {
-    p0.sp = wide_pass_spec(w, 0u, 256u);
+    p0.sp = wide_pass_spec(wf, 0u, 256u);
     if (w.full.base == kRange) {
       // the top digit of a range identifier is the range identifier over the
       // super-bucket splitters s_256, s_512, ... (every 256th splitter)
-      e = cudaMemcpy2DAsync(coarse, 4, w.full.splitters + 255, 1024, 4, w.mc - 1u, cudaMemcpyDeviceToDevice,
-                            c.stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(coarse, 4, w.full.splitters + 255, 1024, 4, w.mc - 1u, cudaMemcpyDeviceToDevice,
+                              c.stream);
       ms_bucket_spec s1{MS_BUCKET_RANGE_U32, w.mc, coarse, 0.f, 0.f, 0u, 0u};
       int k1 = 0;
       if (make_devspec(&s1, &p1.sp, &k1) != MS_OK) e = cudaErrorInvalidValue;
       p1.kind = kRange;
     } else {
-      p1.sp = wide_pass_spec(w, 8u, w.mc);
+      p1.sp = wide_pass_spec(wf, 8u, w.mc);
     }
   }
   if (e == cudaSuccess) e = run_pass(p0, ctx);
@@ -189,7 +237,7 @@ cudaError_t run_wide(const Call& c, const WideSpec& w, DeviceCtx& ctx) {
     if (w.kind == kRadix)
       k_wide_offsets<kRadix><<<blocks, 256, 0, c.stream>>>(c.keys_out, c.n, w.full, w.fm, coff, c.offsets);
     else
-      k_wide_offsets<kWide><<<blocks, 256, 0, c.stream>>>(c.keys_out, c.n, w.full, w.fm, coff, c.offsets);
+      k_wide_offsets<kWide><<<blocks, 256, 0, c.stream>>>(c.keys_out, c.n, wf.full, w.fm, coff, c.offsets);
     e = cudaGetLastError();
   }
   const cudaError_t e2 = scratch_free(ws, c.stream);

@@ -78,3 +78,15 @@ def check_multisplit(keys: np.ndarray, vals, case: Case):
         if not np.array_equal(gv, ov):
             bad = np.nonzero(gv != ov)[0]
             raise AssertionError(f"values differ at {len(bad)} positions, first {bad[:8]} {case} n={len(keys)}")
+
+
+def clustered_splitters(m, seed):
+    """m-1 nondecreasing splitters in tight clusters of 1 to 7 (within 4096 of
+    each other), so that lookup-table cells hold 0, 1, a few or many of them."""
+    g = synthetic.rng(seed)
+    out = []
+    while len(out) < m - 1:
+        base = int(g.integers(0, (1 << 32) - 8192))
+        k = int(g.integers(1, 8))
+        out += [base + int(x) for x in g.integers(0, 4096, size=k)]
+    return np.sort(np.array(out[:m - 1], dtype=np.uint64)).astype(np.uint32)

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synthetic
-from parity import Case, to_dev, to_host
+from parity import Case, clustered_splitters, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -18,11 +18,14 @@ def cases():
     return [Case(oracle.MOD, 32), Case(oracle.RANGE_U32, 8, splitters=synthetic.range_splitters(8, 1)),
             Case(oracle.RADIX, 256, shift=24, bits=8),
             Case(oracle.DELTA_F32, 64, x0=0.0, delta=float(np.float32(1000.0) / np.float32(64))),
-            Case(oracle.MOD, 1)]
+            Case(oracle.MOD, 1),
+            Case(oracle.RANGE_U32, 256, splitters=synthetic.range_splitters(256, 2)),
+            Case(oracle.RANGE_U32, 64, splitters=clustered_splitters(64, 3)),
+            Case(oracle.RANGE_U32, 32, splitters=clustered_splitters(32, 4))]
 
 
 @pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
-@pytest.mark.parametrize("ci", range(5))
+@pytest.mark.parametrize("ci", range(8))
 def test_batch_matches_oracle(ci, pairs):
     import torch
 

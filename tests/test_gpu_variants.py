@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synthetic
-from parity import Case, check_multisplit
+from parity import Case, check_multisplit, clustered_splitters
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +44,33 @@ def test_every_variant_matches_oracle(kind, m):
     log2m = (m - 1).bit_length()
     n = 3 * 4096 + 129
     keys = synthetic.uniform_f32_1000(n, 3) if kind == "delta" else synthetic.uniform_u32(n, 3)
+    try:
+        for shape, rank, reorder in variants(log2m):
+            for pairs in (0, 1):
+                assert ms.ms_tune_set(case.kind, pairs, log2m, ms.ms_tune_size_class(n), shape, rank,
+                                      reorder) == ms.MS_OK
+            check_multisplit(keys, None, case)
+            check_multisplit(keys, synthetic.index_values(n), case)
+    finally:
+        ms.ms_tune_reset()
+
+
+@pytest.mark.parametrize("m", [3, 8, 17, 32, 33, 64, 200, 256])
+def test_every_variant_clustered_splitters(m):
+    """Range buckets whose splitters come in tight clusters: every kernel
+    variant, keys on, just below and just above each splitter, near the
+    clusters and uniform."""
+    import paper_1701_01189_gb300 as ms
+
+    spl = clustered_splitters(m, 70 + m)
+    g = synthetic.rng(71 + m)
+    near = (spl.astype(np.int64)[g.integers(0, m - 1, size=6000)] + g.integers(-4096, 4096, size=6000))
+    keys = np.concatenate([spl, spl - np.uint32(1), spl + np.uint32(1),
+                           np.clip(near, 0, 0xFFFFFFFF).astype(np.uint32), synthetic.uniform_u32(6000, 72)])
+    keys = keys[g.permutation(len(keys))]
+    n = len(keys)
+    case = Case(oracle.RANGE_U32, m, splitters=spl)
+    log2m = (m - 1).bit_length()
     try:
         for shape, rank, reorder in variants(log2m):
             for pairs in (0, 1):

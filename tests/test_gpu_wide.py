@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synthetic
-from parity import Case, check_multisplit, range_case, run_gpu
+from parity import Case, check_multisplit, clustered_splitters, range_case, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -55,6 +55,18 @@ def test_wide_range_duplicate_splitters_and_boundaries(m):
     keys = np.concatenate([spl, spl - np.uint32(1), spl + np.uint32(1), np.array([0, 0xFFFFFFFF], np.uint32),
                            synthetic.uniform_u32(20000, 32)])
     keys = keys[synthetic.rng(33).permutation(len(keys))]
+    check_multisplit(keys, synthetic.index_values(len(keys)), Case(oracle.RANGE_U32, m, splitters=spl))
+
+
+@pytest.mark.parametrize("m", [300, 5000, 65536])
+def test_wide_range_clustered_splitters(m):
+    # clusters of 1 to 7 splitters within 4096: lookup-table cells with 0, 1, a few or many
+    spl = clustered_splitters(m, 34 + m)
+    g = synthetic.rng(35)
+    near = spl.astype(np.int64)[g.integers(0, m - 1, size=50000)] + g.integers(-4096, 4096, size=50000)
+    keys = np.concatenate([spl, spl - np.uint32(1), spl + np.uint32(1), np.clip(near, 0, 0xFFFFFFFF).astype(np.uint32),
+                           synthetic.uniform_u32(50000, 36)])
+    keys = keys[g.permutation(len(keys))]
     check_multisplit(keys, synthetic.index_values(len(keys)), Case(oracle.RANGE_U32, m, splitters=spl))
 
 
