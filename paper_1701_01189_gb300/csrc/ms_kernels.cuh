@@ -136,8 +136,10 @@ __device__ __forceinline__ void rank_windows(const uint32_t* wk, uint32_t avail,
       uint32_t own = vb;
 #pragma unroll
       for (int k = 0; k < NB; ++k) {
-        const uint32_t bal = __ballot_sync(kFull, (b >> k) & 1u);
-        own &= ((b >> k) & 1u) ? bal : ~bal;
+        if ((uint32_t)k < sp.nbits) {  // uniform: only the bits a bucket can have
+          const uint32_t bal = __ballot_sync(kFull, (b >> k) & 1u);
+          own &= ((b >> k) & 1u) ? bal : ~bal;
+        }
       }
       const uint32_t lt = own & lt_mask;
       uint32_t before = 0;
