@@ -185,3 +185,44 @@ def test_section64_distributions(m, dist):
     case = Case(oracle.DELTA_F32, m, x0=0.0, delta=delta)
     check_multisplit(keys, None, case)
     check_multisplit(keys, synthetic.index_values(n), case)
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+@pytest.mark.parametrize("m", [2, 8, 32, 64, 256])
+def test_unaligned_buffers(m, pairs):
+    """Inputs and outputs 4 bytes past a 16-byte boundary: the kernels fall
+    back from bulk and tensor copies to plain loads; the result is the same."""
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+
+    n = 7 * 4096 + 123
+    keys = synthetic.uniform_u32(n, 300 + m)
+    vals = synthetic.index_values(n)
+    case = range_case(m, 301 + m)
+    dk = to_dev(np.concatenate([np.zeros(1, np.uint32), keys]))[1:]
+    dv = to_dev(np.concatenate([np.zeros(1, np.uint32), vals]))[1:]
+    ko = torch.empty(n + 1, dtype=torch.int32, device="cuda")[1:]
+    vo = torch.empty(n + 1, dtype=torch.int32, device="cuda")[1:]
+    assert dk.data_ptr() % 16 == 4 and ko.data_ptr() % 16 == 4
+    spec = case.gpu_spec()
+    if pairs:
+        _, _, off = ms.multisplit_pairs(dk, dv, spec, keys_out=ko, vals_out=vo)
+    else:
+        _, off = ms.multisplit_keys(dk, spec, keys_out=ko)
+    torch.cuda.synchronize()
+    assert ms.device_status() == ms.MS_OK
+    ok, ov, ooff = oracle.multisplit(keys, vals if pairs else None, case.oracle_spec())
+    np.testing.assert_array_equal(to_host(ko), ok)
+    if pairs:
+        np.testing.assert_array_equal(to_host(vo), ov)
+    np.testing.assert_array_equal(to_host(off).astype(np.uint64), ooff)
+    counts = ms.histogram(dk, spec)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_host(counts).astype(np.uint64), np.diff(ooff))
+    sk, sv = ms.radix_sort(dk, dv if pairs else None, 0, 32, keys_out=ko, vals_out=vo if pairs else None)
+    torch.cuda.synchronize()
+    ek, ev = oracle.radix_sort(keys, vals if pairs else None, 0, 32)
+    np.testing.assert_array_equal(to_host(sk), ek)
+    if pairs:
+        np.testing.assert_array_equal(to_host(sv), ev)
