@@ -130,6 +130,7 @@ ms_status make_devspec(const ms_bucket_spec* spec, DevSpec* out, int* kind) {
         return MS_ERR_INVALID_ARG;
       d.x0 = spec->x0;
       d.delta = spec->delta;
+      d.rdelta = 1.0f / spec->delta;
       *kind = kDelta;
       break;
     case MS_BUCKET_RADIX:

@@ -123,6 +123,27 @@ __device__ __forceinline__ uint32_t range_in_cell(uint32_t u, uint32_t e, const 
   return b;
 }
 
+// Delta bucket: floor((x - x0) / delta) with binary32 round-to-nearest
+// subtraction and division, clamped into [0, m-1] (NaN -> m-1).
+// Fast path without the division: with r = delta^-1 rounded, q' = (x - x0) r
+// rounded is q (1 + e1)(1 + e2) for the exact quotient q, |e1|, |e2| <= 2^-24,
+// so it lies within 3.01 |q'| 2^-24 of the rounded quotient fl(q); when q' is
+// farther than q' 2^-22 from every integer (and inside (0, m)), floor(fl(q))
+// is floor(q').  Keys near a bucket edge, negative, infinite or NaN take the
+// division.
+__device__ __forceinline__ uint32_t delta_bucket(uint32_t u, float x0, float delta, float rdelta, uint32_t m) {
+  const float d = __fsub_rn(__uint_as_float(u), x0);
+  const float qa = __fmul_rn(d, rdelta);
+  const float k = floorf(qa);
+  const float fr = __fsub_rn(qa, k);            // exact: qa and k are within a factor of two (or k = 0)
+  const float eps = __fmul_rn(qa, 0x1p-22f);  // exact: a power of two
+  if (qa > 0.0f && qa < (float)m && fr > eps && __fsub_rn(1.0f, fr) > eps) return (uint32_t)k;
+  const float f = floorf(__fdiv_rn(d, delta));  // IEEE round-to-nearest
+  if (!(f < (float)m)) return m - 1u;           // f >= m, +inf, NaN
+  if (f <= 0.0f) return 0u;                     // negative, -0, -inf
+  return (uint32_t)f;
+}
+
 // Table of the super-bucket splitters of a wide range identifier: entry i is
 // s_{256(i+1)}, the first splitter of super-bucket i+1 (mc - 1 of them),
 // padded with 0xffffffff to 2^NB - 1 entries.  The count of these <= u is
@@ -179,9 +200,7 @@ __device__ __forceinline__ uint32_t wide_bucket(uint32_t u, const DevSpec& sp, c
       b = 256u * S + pos;
     }
   } else if (sp.base == kDelta) {
-    const float x = __uint_as_float(u);
-    const float f = floorf(__fdiv_rn(__fsub_rn(x, sp.x0), sp.delta));
-    b = !(f < (float)sp.fm) ? sp.fm - 1u : (f <= 0.0f ? 0u : (uint32_t)f);
+    b = delta_bucket(u, sp.x0, sp.delta, sp.rdelta, sp.fm);
   } else {
     const uint32_t t = __umulhi(sp.mod_magic, u);
     const uint32_t q = (t + ((u - t) >> sp.mod_sh1)) >> sp.mod_sh2;
@@ -220,12 +239,7 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t u, const DevSpec& sp, con
       return packed_fast<NB>(u, e, (1u << sh) - 1u);
     }
   } else if constexpr (KIND == kDelta) {
-    const float x = __uint_as_float(u);
-    const float q = __fdiv_rn(__fsub_rn(x, sp.x0), sp.delta);  // IEEE round-to-nearest
-    const float f = floorf(q);
-    if (!(f < (float)sp.m)) return sp.m - 1;  // f >= m, +inf, NaN
-    if (f <= 0.0f) return 0u;                 // negative, -0, -inf
-    return (uint32_t)f;
+    return delta_bucket(u, sp.x0, sp.delta, sp.rdelta, sp.m);
   } else if constexpr (KIND == kRadix) {
     return (u >> sp.shift) & sp.mask;
   } else if constexpr (KIND == kWide) {

@@ -43,6 +43,7 @@ struct DevSpec {
   uint32_t nbits;             // ceil(log2 m); 0 when m == 1
   const uint32_t* splitters;  // kRange: m-1 nondecreasing values (device)
   float x0, delta;            // kDelta
+  float rdelta;               // kDelta: 1 / delta rounded to binary32 (the fast path of delta_bucket)
   uint32_t shift, mask;       // kRadix: shift < 32
   uint32_t mod_magic, mod_sh1, mod_sh2;  // kMod: multiply-shift constants
   uint32_t m_pad;             // m rounded up to a multiple of 32 (at least 32)

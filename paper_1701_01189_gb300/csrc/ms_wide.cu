@@ -142,6 +142,7 @@ ms_status make_wide_spec(const ms_bucket_spec* spec, WideSpec* out) {
       if (!std::isfinite(spec->x0) || !std::isfinite(spec->delta) || !(spec->delta > 0.0f)) return MS_ERR_INVALID_ARG;
       d.x0 = spec->x0;
       d.delta = spec->delta;
+      d.rdelta = 1.0f / spec->delta;
       d.base = kDelta;
       w.kind = kWide;
       break;

@@ -83,6 +83,26 @@ def test_delta_f32(m):
     check_multisplit(keys, None, Case(oracle.DELTA_F32, m, x0=-3.5, delta=float(delta) * 0.75))
 
 
+@pytest.mark.parametrize("m", [3, 7, 100, 256, 1000, 65536])
+def test_delta_f32_every_bucket_edge(m):
+    """Keys on every bucket edge k * delta and up to four ulps either side
+    (the division's rounding decides their bucket), for deltas that are not
+    exact in binary32 and for an offset x0; m above 256 takes the digit passes."""
+    for x0, scale in ((0.0, 1.0), (-3.5, 0.75)):
+        delta = np.float32(np.float32(1000.0) / np.float32(m) * np.float32(scale))
+        edge = (np.float32(x0) + np.arange(m + 1, dtype=np.float32) * delta).astype(np.float32)
+        near = [edge]
+        lo = hi = edge
+        for _ in range(4):
+            lo = np.nextafter(lo, np.float32(-np.inf)).astype(np.float32)
+            hi = np.nextafter(hi, np.float32(np.inf)).astype(np.float32)
+            near += [lo, hi]
+        keys = np.concatenate([np.concatenate(near).view(np.uint32), synthetic.uniform_f32_1000(50_000, m)])
+        keys = keys[synthetic.rng(m).permutation(len(keys))]
+        check_multisplit(keys, synthetic.index_values(len(keys)),
+                         Case(oracle.DELTA_F32, m, x0=x0, delta=float(delta)))
+
+
 @pytest.mark.parametrize("pattern", ["same", "sorted", "reversed", "one_bucket", "alternating"])
 @pytest.mark.parametrize("m", [2, 32, 256])
 def test_patterns(pattern, m):
