@@ -200,7 +200,10 @@ __device__ __forceinline__ uint32_t wide_bucket(uint32_t u, const DevSpec& sp, c
       b = 256u * S + pos;
     }
   } else if (sp.base == kDelta) {
-    b = delta_bucket(u, sp.x0, sp.delta, sp.rdelta, sp.fm);
+    // always the division: with up to 2^16 buckets the edge margin of
+    // delta_bucket's fast path catches enough keys that most warps run both
+    const float f = floorf(__fdiv_rn(__fsub_rn(__uint_as_float(u), sp.x0), sp.delta));
+    b = !(f < (float)sp.fm) ? sp.fm - 1u : (f <= 0.0f ? 0u : (uint32_t)f);
   } else {
     const uint32_t t = __umulhi(sp.mod_magic, u);
     const uint32_t q = (t + ((u - t) >> sp.mod_sh1)) >> sp.mod_sh2;
