@@ -32,6 +32,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -85,10 +86,10 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir: str):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}_{os.getpid()}.csv")
+        self.path = os.path.join(out_dir, f"clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -241,7 +242,7 @@ def run_gpu(args, rank: int, world: int):
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in case_list] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", torch.cuda.current_device())))
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", torch.cuda.current_device())), args.clocks_dir)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -691,6 +692,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                    help="where the nvidia-smi clock samples of the timed region are written")
     ap.add_argument("--no-extras", action="store_true", help="skip the radix-sort, batched and serving configurations")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving trace (0: skip)")
     args = ap.parse_args()
