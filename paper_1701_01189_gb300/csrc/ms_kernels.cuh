@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
           if (p < T) {
             s_keys[p] = rk[off0 + i * 32];
             if constexpr (PAIRS) s_vals[p] = rv[off0 + i * 32];
-            s_bkt[p] = (uint8_t)b;
+            if constexpr (!cheap_bucket<KIND>()) s_bkt[p] = (uint8_t)b;
           } else {
             atomicOr(a.err, kDevErrBounds);
           }
@@ -397,9 +397,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
       for (int k = 0; k < ITEMS; ++k) {
         const uint32_t p = threadIdx.x + k * THREADS;
         if (FULL || p < tile_n) {
-          const uint32_t g = s_delta[s_bkt[p]] + p;
+          const uint32_t kq = s_keys[p];
+          uint32_t b;
+          if constexpr (cheap_bucket<KIND>())
+            b = bucket_of<KIND, NB>(kq, sp, s_tbl, s_lut);
+          else
+            b = s_bkt[p];
+          const uint32_t g = s_delta[b] + p;
           if (g < a.n) {
-            __stcs(a.keys_out + g, s_keys[p]);
+            __stcs(a.keys_out + g, kq);
             if constexpr (PAIRS) __stcs(a.vals_out + g, s_vals[p]);
           } else {
             atomicOr(a.err, kDevErrBounds);

@@ -106,7 +106,8 @@ struct OnesweepArgs {
 
 // Shared memory (words): a ring of two slots (keys T, then values T for
 // pairs), s_goff 256, s_delta 256, s_warp 32, s_cnt NW*257, s_peer
-// 2*NW*256, bucket bytes T.  The tile is permuted in place in its slot.
+// 2*NW*256.  The tile is permuted in place in its slot; the write-out takes
+// each key's digit from the key again.
 template <bool PAIRS>
 struct OsLayout {
   static constexpr uint32_t T = kOsTile;
@@ -116,8 +117,7 @@ struct OsLayout {
   static constexpr uint32_t kWarp = kDelta + 256;
   static constexpr uint32_t kCnt = kWarp + 32;
   static constexpr uint32_t kPeer = kCnt + kOsNW * 257;
-  static constexpr uint32_t kBkt = (kPeer + 2 * kOsNW * 256 + 3) & ~3u;
-  static constexpr size_t kBytes = 4u * (size_t)kBkt + T;
+  static constexpr size_t kBytes = 4u * (size_t)(kPeer + 2 * kOsNW * 256);
 };
 
 // One digit pass, persistent: every CTA takes tiles by ticket (so every
@@ -138,7 +138,6 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
   uint32_t* s_warp = smem + Lay::kWarp;
   uint32_t* s_cnt = smem + Lay::kCnt;
   uint32_t* s_peer = smem + Lay::kPeer;
-  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(smem + Lay::kBkt);
   const DevSpec& sp = a.sp;
   const uint32_t m = sp.m, m_pad = sp.m_pad, S = m_pad + 1;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
@@ -298,7 +297,6 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
         if (p < T) {
           sk[p] = kr[i];
           if constexpr (PAIRS) sv[p] = vr[i];
-          s_bkt[p] = (uint8_t)b;
         } else {
           atomicOr(a.err, kDevErrBounds);
         }
@@ -309,16 +307,17 @@ __global__ void __launch_bounds__(kOsNW * 32, PAIRS ? 2 : 3) k_onesweep_pass(One
     for (int q = 0; q < kOsItems; ++q) {
       const uint32_t p = threadIdx.x + q * THREADS;
       if (p < tile_n) {
-        const uint32_t g = s_delta[s_bkt[p]] + p;
+        const uint32_t kq = sk[p];
+        const uint32_t g = s_delta[(kq >> a.sp.shift) & a.sp.mask] + p;  // the digit again: two instructions
         if (g < a.n) {
-          __stcs(a.keys_out + g, sk[p]);
+          __stcs(a.keys_out + g, kq);
           if constexpr (PAIRS) __stcs(a.vals_out + g, sv[p]);
         } else {
           atomicOr(a.err, kDevErrBounds);
         }
       }
     }
-    __syncthreads();  // the slot, s_bkt and s_delta are free again
+    __syncthreads();  // the slot and s_delta are free again
   }
 }
 

@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
         if (p < T) {
           sk[tc_rswz(p)] = key[i];
           if constexpr (PAIRS) sv[tc_rswz(p)] = val[i];
-          s_bkt[tc_rswz(p)] = (uint8_t)bk[i];
+          if constexpr (!cheap_bucket<KIND>()) s_bkt[tc_rswz(p)] = (uint8_t)bk[i];
         } else {
           atomicOr(a.err, kDevErrBounds);
         }
@@ -618,9 +618,17 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
       const uint32_t p = t + k * kTcThreads;
       if (FULL || p < tile_n) {
         const uint32_t q = tc_rswz(p);
-        const uint32_t g = s_delta[s_bkt[q]] + p;
+        const uint32_t kq = sk[q];
+        uint32_t b;
+        if constexpr (cheap_bucket<KIND>()) {
+          uint32_t unused = 0;
+          b = tc_bucket<KIND>(kq, sp, L, unused);
+        } else {
+          b = s_bkt[q];
+        }
+        const uint32_t g = s_delta[b] + p;
         if (g < a.n) {
-          __stcs(a.keys_out + g, sk[q]);
+          __stcs(a.keys_out + g, kq);
           if constexpr (PAIRS) __stcs(a.vals_out + g, sv[q]);
         } else {
           atomicOr(a.err, kDevErrBounds);
