@@ -208,7 +208,7 @@ def test_section64_distributions(m, dist):
 
 
 @pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
-@pytest.mark.parametrize("m", [2, 8, 32, 64, 256])
+@pytest.mark.parametrize("m", [2, 8, 32, 64, 256, 1000])
 def test_unaligned_buffers(m, pairs):
     """Inputs and outputs 4 bytes past a 16-byte boundary: the kernels fall
     back from bulk and tensor copies to plain loads; the result is the same."""
@@ -237,9 +237,10 @@ def test_unaligned_buffers(m, pairs):
     if pairs:
         np.testing.assert_array_equal(to_host(vo), ov)
     np.testing.assert_array_equal(to_host(off).astype(np.uint64), ooff)
-    counts = ms.histogram(dk, spec)
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(to_host(counts).astype(np.uint64), np.diff(ooff))
+    if m <= ms.MAX_M:
+        counts = ms.histogram(dk, spec)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_host(counts).astype(np.uint64), np.diff(ooff))
     sk, sv = ms.radix_sort(dk, dv if pairs else None, 0, 32, keys_out=ko, vals_out=vo if pairs else None)
     torch.cuda.synchronize()
     ek, ev = oracle.radix_sort(keys, vals if pairs else None, 0, 32)
