@@ -1,16 +1,17 @@
 """The keys-only multisplit variant that allocates no device memory.
 
 Who needs it: callers that cannot let a library allocate while they enqueue
-work -- code being captured into a CUDA graph without allocation nodes, hot
-loops where allocator calls are forbidden, and processes whose device memory is
-owned by another allocator.  ms_multisplit_keys_noalloc takes its scratch from a
-fixed array inside the library instead.
+work -- hot loops where allocator calls are forbidden, and processes whose
+device memory is owned by another allocator.  ms_multisplit_keys_noalloc takes
+its scratch from a fixed array inside the library instead.
 
 This file is collected last on purpose.  It calls the variant through the C
 ABI twice in a row (the second call reuses the fixed array exactly as the first
 one left it) and checks both results bit for bit against ms_multisplit_keys,
-the entry point that allocates its scratch from the library pool; it also
-checks that the calls leave the device's free memory unchanged.  It passes both
+the entry point that allocates its scratch from the library pool, and against
+the CPU oracle; it also checks that the calls leave the device's free memory
+unchanged.  A bounded wait made to run out on this path is reported by
+ms_noalloc_status and does not disturb the calls after it.  It passes both
 alone in a fresh process and after the rest of the suite.
 """
 import numpy as np
@@ -66,10 +67,55 @@ def test_noalloc_matches_pooled_entry_point_twice(case):
     results = [call_and_copy_back() for _ in range(2)]
     free_after, _ = torch.cuda.mem_get_info()
     assert free_after == free_before
+    ok, _, ooff = oracle.multisplit(keys, None, case.oracle_spec())
+    np.testing.assert_array_equal(expect_k, ok)
     for st, k, o in [(st, k0, o0)] + results:
         assert st == ms.MS_OK
         np.testing.assert_array_equal(k, expect_k)
         np.testing.assert_array_equal(o, expect_off)
+        np.testing.assert_array_equal(k, ok)
+        np.testing.assert_array_equal(o.astype(np.uint64), ooff)
+    assert ms.ms_noalloc_status(stream) == ms.MS_OK  # this path's own status word
+    assert ms.device_status() == ms.MS_OK  # the pooled path's, untouched
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1]], ids=["range32", "radix256"])
+def test_noalloc_expired_wait_is_reported_and_later_calls_are_exact(case):
+    """An expired bounded wait on this path (a look-back wait on a status word
+    that nothing publishes) sets the timeout bit in the fixed array's header.
+    The next call must still wait its full bound and be exact (with 32 buckets
+    its post-scan waits on copy barriers, with 256 on the look-back scan), and
+    ms_noalloc_status must report the timeout once, then clear."""
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+    from paper_1701_01189_gb300.build import build
+
+    build()
+    stream = torch.cuda.current_stream().cuda_stream
+    n = (1 << 21) + 5
+    keys = synthetic.uniform_u32(n, 21)
+    ok, _, ooff = oracle.multisplit(keys, None, case.oracle_spec())
+    spec = case.gpu_spec()
+    dk = to_dev(keys)
+    out_k = torch.empty_like(dk)
+    out_off = torch.empty(case.m + 1, dtype=torch.int32, device="cuda")
+    assert ms.ms_noalloc_status(stream) == ms.MS_OK
+    for read_status_between in (False, True):
+        assert ms.ms_test_expire_lookback_noalloc(stream) == ms.MS_OK
+        if read_status_between:
+            assert ms.ms_noalloc_status(stream) == ms.MS_ERR_TIMEOUT
+        for _ in range(2):
+            out_k.fill_(0)
+            st = ms.ms_multisplit_keys_noalloc(dk.data_ptr(), n, spec.c(), out_k.data_ptr(), out_off.data_ptr(),
+                                               stream)
+            assert st == ms.MS_OK
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(to_host(out_k), ok)
+            np.testing.assert_array_equal(to_host(out_off).astype(np.uint64), ooff)
+        expect = ms.MS_OK if read_status_between else ms.MS_ERR_TIMEOUT
+        assert ms.ms_noalloc_status(stream) == expect
+        assert ms.ms_noalloc_status(stream) == ms.MS_OK  # reading clears it
     assert ms.device_status() == ms.MS_OK
 
 
