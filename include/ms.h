@@ -125,26 +125,45 @@ ms_status ms_histogram(const uint32_t *keys, size_t n, const ms_bucket_spec *spe
 
 /* Keys-only stable multisplit that allocates nothing (the paper has no
  * counterpart; this is a deployment variant of ms_multisplit_keys).  For
- * callers that must not allocate device memory during the call: work being
- * captured into a CUDA graph without allocation nodes, hot loops that forbid
- * allocator calls, or processes whose device memory is owned by another
- * allocator.  Same arguments, result and argument errors as
+ * callers that must not allocate device memory during the call: hot loops
+ * that forbid allocator calls, or processes whose device memory is owned by
+ * another allocator.  Same arguments, result and argument errors as
  * ms_multisplit_keys; the scratch comes from a fixed 1 MiB array in device
  * memory that every GPU loading the library holds until exit.
  *   - The first call on each device (with it current) looks up the array's
- *     device address and sets up the kernels; make it before any stream
- *     capture.  It allocates nothing.
+ *     device address; the first call that uses a given kernel variant (picked
+ *     by the bucket kind, m and the size class of n) sets that kernel's
+ *     attributes and queries its occupancy.  Make these first calls before any
+ *     stream capture.  None of this allocates.
  *   - All calls share the array: calls that overlap on the GPU race and
  *     corrupt each other's results; serialize them (one stream, or events).
  *   - The scratch must hold 4*m*G + 16 bytes, plus 8*ceil(m*G/4096) for
  *     m > 32 (G = CTAs of the launch, at most SMs x resident CTAs per SM;
- *     about 610 KiB at most on a 152-SM GB300).  A call needing more gets MS_ERR_OUT_OF_MEMORY and
- *     nothing is enqueued.
+ *     about 610 KiB at most on a 152-SM GB300).  A call needing more gets
+ *     MS_ERR_OUT_OF_MEMORY and its outputs are not touched.
  *   - Device-side failures (an expired bounded wait, a failed bounds check)
- *     are recorded in a word of the fixed array and are not reported by
- *     ms_device_status(). */
+ *     are recorded in a header word of the fixed array, not in the word
+ *     ms_device_status() reads: ms_noalloc_status() reports them.  Each call
+ *     starts from a clear word, so a failure never shortens the waits of a
+ *     later call. */
 ms_status ms_multisplit_keys_noalloc(const uint32_t *keys_in, size_t n, const ms_bucket_spec *spec,
                                      uint32_t *keys_out, uint32_t *offsets, void *stream);
+
+/* Reads and clears the device-side status of ms_multisplit_keys_noalloc on
+ * the calling device (no counterpart in the paper): MS_OK, MS_ERR_TIMEOUT if a
+ * bounded wait of any such call expired since the last read, MS_ERR_CUDA for
+ * another recorded failure (a failed bounds check) or a failed CUDA call.
+ * Synchronizes `stream` first; covers every call enqueued before that point. */
+ms_status ms_noalloc_status(void *stream);
+
+/* Failure-path test aid of the entry point above (no counterpart in the
+ * paper): enqueues on `stream` the look-back scan kernel as the second of two
+ * scan tiles on the fixed array's scratch, with the first tile's status never
+ * published, so its bounded wait runs out (after about a quarter of a second)
+ * and records MS_ERR_TIMEOUT exactly where an expired wait inside
+ * ms_multisplit_keys_noalloc would.  Shares the array with that entry point:
+ * serialize it with those calls. */
+ms_status ms_test_expire_lookback_noalloc(void *stream);
 
 /* ---- Batched multisplit: many independent arrays in one persistent launch.
  * Not in the paper (it runs one problem per launch); the same method applied
@@ -205,6 +224,34 @@ ms_status ms_batch_run_graph(ms_batch_plan *plan, void *stream);
 
 /* Waits for the device, then frees the plan (NULL is fine). */
 ms_status ms_batch_plan_destroy(ms_batch_plan *plan);
+
+/* The batched multisplit in one call, over segment descriptors that live in
+ * DEVICE memory (the batching form of Section 3.1's multisplit; the paper
+ * runs one problem per launch).  segs_dev: device array of num_segments
+ * ms_segment, all keys-only or all key-value as for ms_batch_plan_create.
+ * offsets: device array of num_segments * (m + 1) words, segment i's bucket
+ * starts at offsets[i * (m + 1)] (then each descriptor's own `offsets` field
+ * is ignored), or NULL to use the descriptors' fields.  The call reads the
+ * descriptors back to the host -- it synchronizes `stream` for that -- builds
+ * the work list, and enqueues one memset and one persistent launch on
+ * `stream` through a plan the library keeps per (device, spec, keys-only or
+ * key-value) and grows as needed; spec->splitters must stay valid until that
+ * work is done.  Calls that reuse a cached plan are ordered one after another
+ * on the GPU even from different streams.  Each segment's result equals
+ * ms_multisplit_keys / ms_multisplit_pairs on it.  Errors as for
+ * ms_batch_plan_create, checked before anything is enqueued. */
+ms_status ms_multisplit_pairs_batched(const ms_segment *segs_dev, uint32_t num_segments,
+                                      const ms_bucket_spec *spec, uint32_t *offsets, void *stream);
+
+/* Releases what the library holds on every device it has used: the scratch
+ * memory pool, the device status word, the plans cached by
+ * ms_multisplit_pairs_batched, and the stage-timing events.  Waits for each
+ * of those devices first.  A later call starts afresh (it creates the state
+ * again).  Returns MS_ERR_INVALID_ARG, and releases nothing, while a batch plan
+ * made by the caller is still alive (destroy it first).  Safe to call twice;
+ * must not run concurrently with other calls of this library.  The fixed
+ * array of ms_multisplit_keys_noalloc is part of the loaded library and stays. */
+ms_status ms_shutdown(void);
 
 /* Reads and clears the calling device's status word: MS_OK, or
  * MS_ERR_TIMEOUT if any bounded device-side wait expired since the last read.

@@ -105,6 +105,13 @@ def lib() -> ctypes.CDLL:
             getattr(L, f).restype = ctypes.c_int
         L.ms_test_expire_lookback.argtypes = [P]
         L.ms_test_expire_lookback.restype = ctypes.c_int
+        L.ms_test_expire_lookback_noalloc.argtypes = [P]
+        L.ms_noalloc_status.argtypes = [P]
+        L.ms_shutdown.argtypes = []
+        L.ms_multisplit_pairs_batched.argtypes = [P, ctypes.c_uint32, SP, P, P]
+        for f in ("ms_test_expire_lookback_noalloc", "ms_noalloc_status", "ms_shutdown",
+                  "ms_multisplit_pairs_batched"):
+            getattr(L, f).restype = ctypes.c_int
         L.ms_stage_timing.argtypes = [I]
         L.ms_stage_times.argtypes = [P, P, P, P]
         for f in ("ms_multisplit_keys", "ms_multisplit_pairs", "ms_multisplit_keys_noalloc", "ms_radix_sort",
@@ -150,6 +157,32 @@ def ms_device_status(stream: int) -> int:
 
 def ms_test_expire_lookback(stream: int) -> int:
     return lib().ms_test_expire_lookback(stream)
+
+
+def ms_test_expire_lookback_noalloc(stream: int) -> int:
+    return lib().ms_test_expire_lookback_noalloc(stream)
+
+
+def ms_noalloc_status(stream: int) -> int:
+    return lib().ms_noalloc_status(stream)
+
+
+def ms_shutdown() -> int:
+    return lib().ms_shutdown()
+
+
+def ms_multisplit_pairs_batched(segs_dev: int, num_segments: int, spec: "_Spec", offsets: int, stream: int) -> int:
+    """segs_dev: device address of num_segments ms_segment records (see segment_records)."""
+    return lib().ms_multisplit_pairs_batched(segs_dev, num_segments, ctypes.byref(spec), offsets, stream)
+
+
+def segment_records(segs) -> bytes:
+    """The bytes of an ms_segment array for (keys_in, vals_in, keys_out, vals_out, offsets, n) tuples,
+    to be copied to the device for ms_multisplit_pairs_batched."""
+    arr = (_Segment * max(1, len(segs)))()
+    for i, s in enumerate(segs):
+        arr[i] = _Segment(*s)
+    return bytes(arr)[:ctypes.sizeof(_Segment) * len(segs)]
 
 
 def ms_stage_timing(enable: int) -> int:

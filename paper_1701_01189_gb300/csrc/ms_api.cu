@@ -368,6 +368,31 @@ extern "C" ms_status ms_test_expire_lookback(void* stream) {
   return to_status(e != cudaSuccess ? e : e2);
 }
 
+extern "C" ms_status ms_shutdown(void) {
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return MS_ERR_CUDA;
+  // a caller's batch plan refers to its device's status word: refuse while one is alive
+  for (int dev = 0; dev < 64; ++dev)
+    if (batch_live_plans(dev) > 0) return MS_ERR_INVALID_ARG;
+  for (int dev = 0; dev < 64; ++dev) batch_cache_release(dev);
+  ms_status st = MS_OK;
+  {
+    std::lock_guard<std::mutex> lock(g_ctx_mu);
+    for (int dev = 0; dev < 64; ++dev) {
+      DeviceCtx& c = g_ctx[dev];
+      if (c.device < 0) continue;
+      if (cudaSetDevice(dev) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) st = MS_ERR_CUDA;
+      if (c.d_err != nullptr && cudaFree(c.d_err) != cudaSuccess) st = MS_ERR_CUDA;
+      if (c.pool != nullptr && cudaMemPoolDestroy(c.pool) != cudaSuccess) st = MS_ERR_CUDA;
+      c = DeviceCtx();
+    }
+  }
+  trace_release();
+  if (cudaSetDevice(cur) != cudaSuccess) st = MS_ERR_CUDA;
+  if (st != MS_OK) cudaGetLastError();
+  return st;
+}
+
 extern "C" ms_status ms_device_status(void* stream) {
   DeviceCtx* ctx = nullptr;
   ms_status st = current_ctx(&ctx);

@@ -17,6 +17,7 @@
 // that flag (bounded).  Every item a CTA waits for has an earlier ticket, so
 // it belongs to a CTA that is already running: the waits always end.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -327,8 +328,13 @@ static cudaError_t batch_call(ms_batch_plan& p, int sm_count, cudaStream_t s, bo
   }
 }
 
+// Plans alive per device (ms_shutdown refuses to run while a caller's plan
+// still refers to the device's status word).
+static std::atomic<int> g_live_plans[64];
+
 static void plan_free(ms_batch_plan* p) {
   if (p == nullptr) return;
+  if (p->device >= 0 && p->device < 64) g_live_plans[p->device].fetch_sub(1);
   if (p->graph) cudaGraphExecDestroy(p->graph);
   for (int k = 0; k < 2; ++k) {
     if (p->stage_done[k]) cudaEventDestroy(p->stage_done[k]);
@@ -395,6 +401,7 @@ static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec&
 static ms_status plan_alloc(ms_batch_plan* p, DeviceCtx* ctx, int kind, bool pairs, const DevSpec& sp,
                             uint32_t max_segments, uint32_t max_items, uint64_t max_hwords) {
   p->device = ctx->device;
+  if (p->device >= 0 && p->device < 64) g_live_plans[p->device].fetch_add(1);
   p->kind = kind;
   p->pairs = pairs;
   p->sp = sp;
@@ -557,4 +564,144 @@ extern "C" ms_status ms_batch_plan_destroy(ms_batch_plan* plan) {
   }
   plan_free(plan);
   return MS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One call over device-resident segment descriptors.  The descriptors are
+// read back to the host (the work list is built there, as for the plans
+// above), then the work runs through a dynamic plan kept in a small
+// per-process cache keyed by device, bucket spec and keys-only / key-value,
+// and grown when a call needs more segments or elements than it holds.
+namespace ms {
+namespace {
+struct CachedPlan {
+  int device;
+  bool pairs;
+  ms_bucket_spec spec;
+  uint32_t max_segments;
+  uint64_t max_elements;
+  ms_batch_plan* plan;
+  cudaEvent_t last_run;  // recorded after the plan's latest run
+  uint64_t stamp;        // least recently used is evicted first
+};
+std::mutex g_cache_mu;
+std::vector<CachedPlan> g_cache;
+uint64_t g_cache_clock = 0;
+constexpr size_t kCacheEntries = 8;
+
+bool same_spec(const ms_bucket_spec& a, const ms_bucket_spec& b) {
+  return a.kind == b.kind && a.m == b.m && a.splitters == b.splitters && a.x0 == b.x0 && a.delta == b.delta &&
+         a.shift == b.shift && a.bits == b.bits;
+}
+
+void release_entry(CachedPlan& c) {
+  if (c.last_run) {
+    cudaEventSynchronize(c.last_run);
+    cudaEventDestroy(c.last_run);
+  }
+  plan_free(c.plan);
+  c.plan = nullptr;
+  c.last_run = nullptr;
+}
+
+uint64_t round_up_pow2(uint64_t v, uint64_t floor_v) {
+  uint64_t r = floor_v;
+  while (r < v) r <<= 1;
+  return r;
+}
+}  // namespace
+
+int batch_live_plans(int dev) {
+  if (dev < 0 || dev >= 64) return 0;
+  int cached = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    for (const auto& c : g_cache) cached += c.device == dev ? 1 : 0;
+  }
+  return g_live_plans[dev].load() - cached;
+}
+
+void batch_cache_release(int dev) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  for (auto& c : g_cache)
+    if (c.device == dev) release_entry(c);
+  g_cache.erase(std::remove_if(g_cache.begin(), g_cache.end(), [](const CachedPlan& c) { return c.plan == nullptr; }),
+                g_cache.end());
+}
+
+}  // namespace ms
+
+extern "C" ms_status ms_multisplit_pairs_batched(const ms_segment* segs_dev, uint32_t num_segments,
+                                                 const ms_bucket_spec* spec, uint32_t* offsets, void* stream) {
+  DevSpec sp;
+  int kind = 0;
+  ms_status st = make_devspec(spec, &sp, &kind);
+  if (st != MS_OK) return st;
+  if (num_segments == 0) return MS_OK;
+  if (segs_dev == nullptr) return MS_ERR_INVALID_ARG;
+  DeviceCtx* ctx = nullptr;
+  st = current_device_ctx(&ctx);
+  if (st != MS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<ms_segment> segs(num_segments);
+  cudaError_t e = cudaMemcpyAsync(segs.data(), segs_dev, num_segments * sizeof(ms_segment), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return to_status(e);
+  bool pairs = false;
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < num_segments; ++i) {
+    if (offsets != nullptr) segs[i].offsets = offsets + (size_t)i * (sp.m + 1);
+    if (segs[i].n >= ((size_t)1 << 32)) return MS_ERR_INVALID_ARG;
+    pairs = pairs || (segs[i].n > 0 && segs[i].vals_in != nullptr);
+    total += segs[i].n;
+  }
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  CachedPlan* hit = nullptr;
+  for (auto& c : g_cache)
+    if (c.device == ctx->device && c.pairs == pairs && same_spec(c.spec, *spec) && c.max_segments >= num_segments &&
+        c.max_elements >= total)
+      hit = &c;
+  if (hit == nullptr) {
+    // a new plan, a little larger than needed so that nearby calls reuse it;
+    // replaces a smaller one for the same spec, else the least recently used
+    CachedPlan c;
+    std::memset(&c, 0, sizeof c);
+    c.device = ctx->device;
+    c.pairs = pairs;
+    c.spec = *spec;
+    c.max_segments = (uint32_t)round_up_pow2(num_segments, 64);
+    c.max_elements = round_up_pow2(total, (uint64_t)1 << 20);
+    st = ms_batch_plan_create_dynamic(c.max_segments, c.max_elements, pairs ? 1 : 0, spec, &c.plan);
+    if (st != MS_OK) return st;
+    if (cudaEventCreateWithFlags(&c.last_run, cudaEventDisableTiming) != cudaSuccess) {
+      plan_free(c.plan);
+      return to_status(cudaGetLastError());
+    }
+    size_t victim = g_cache.size();
+    for (size_t i = 0; i < g_cache.size(); ++i)
+      if (g_cache[i].device == c.device && g_cache[i].pairs == pairs && same_spec(g_cache[i].spec, *spec)) victim = i;
+    if (victim == g_cache.size() && g_cache.size() >= kCacheEntries) {
+      victim = 0;
+      for (size_t i = 1; i < g_cache.size(); ++i)
+        if (g_cache[i].stamp < g_cache[victim].stamp) victim = i;
+    }
+    if (victim < g_cache.size()) {
+      release_entry(g_cache[victim]);
+      g_cache[victim] = c;
+      hit = &g_cache[victim];
+    } else {
+      g_cache.push_back(c);
+      hit = &g_cache.back();
+    }
+  }
+  hit->stamp = ++g_cache_clock;
+  // the plan's previous run (possibly on another stream) reads the segment
+  // table and work list that the upload below replaces
+  e = cudaStreamWaitEvent(s, hit->last_run, 0);
+  if (e != cudaSuccess) return to_status(e);
+  st = ms_batch_plan_set_segments(hit->plan, segs.data(), num_segments, stream);
+  if (st != MS_OK) return st;
+  st = ms_batch_run(hit->plan, stream);
+  if (st != MS_OK) return st;
+  return to_status(cudaEventRecord(hit->last_run, s));
 }

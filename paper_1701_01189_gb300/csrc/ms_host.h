@@ -96,6 +96,13 @@ cudaError_t run_wide(const Call& c, const WideSpec& w, DeviceCtx& ctx);
 cudaError_t run_onesweep_sort(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t n, int begin_bit, int end_bit,
                               uint32_t* keys_out, uint32_t* vals_out, cudaStream_t s, DeviceCtx& ctx);
 
+// Batch plans alive on a device, not counting the library's own cached plans
+// of ms_multisplit_pairs_batched (ms_batch.cu), and the release of those.
+int batch_live_plans(int dev);
+void batch_cache_release(int dev);
+// Releases the stage-timing events (ms_trace.cu).
+void trace_release();
+
 // Scratch from the library pool, ordered on `stream`.
 cudaError_t scratch_alloc(DeviceCtx& ctx, void** p, size_t bytes, cudaStream_t stream);
 cudaError_t scratch_free(void* p, cudaStream_t stream);

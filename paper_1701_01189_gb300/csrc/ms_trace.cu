@@ -41,6 +41,16 @@ void trace_mark(int slot, int stage, cudaStream_t s) {
   if (slot < (int)g_used.size()) cudaEventRecord(g_used[slot].ev[stage], s);
 }
 
+void trace_release() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_on = false;
+  for (auto* v : {&g_used, &g_free})
+    for (auto& q : *v)
+      for (auto& e : q.ev) cudaEventDestroy(e);
+  g_used.clear();
+  g_free.clear();
+}
+
 }  // namespace ms
 
 using namespace ms;
