@@ -30,6 +30,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import tempfile
@@ -590,6 +591,8 @@ def extras_gpu(args, ms, metrics, torch, dev):
     try:
         t_graph = _time(torch, lambda: ms.ms_batch_run_graph(plan, sptr), reps=5)
         t_launch = _time(torch, lambda: ms.ms_batch_run(plan, sptr), reps=5)
+        # outside the timed regions: the batched outputs must equal one plain launch per segment
+        b_k, b_v, b_o = ko_all.clone(), vo_all.clone(), offs.clone()
 
         def plain():
             for (kin, vin, kout, vout, off, n_) in segs:
@@ -598,6 +601,10 @@ def extras_gpu(args, ms, metrics, torch, dev):
                     raise ms.MsError(st, "plain")
 
         t_plain = _time(torch, plain, reps=2, warmup=1)
+        torch.cuda.synchronize()
+        if not (torch.equal(b_k, ko_all) and torch.equal(b_v, vo_all) and torch.equal(b_o, offs)):
+            raise RuntimeError("batched outputs differ from the per-segment plain launches")
+        del b_k, b_v, b_o
     finally:
         ms.ms_batch_plan_destroy(plan)
     comp = metrics.sol_rate_g(peak, metrics.compulsory_bytes_per_element(True))
@@ -606,7 +613,7 @@ def extras_gpu(args, ms, metrics, torch, dev):
         "plain_per_segment_ms": round(t_plain, 3),
         "gpairs_s_graph": round(metrics.rate_g(total, t_graph * 1e-3), 2),
         "gpairs_s_plain": round(metrics.rate_g(total, t_plain * 1e-3), 2),
-        "speedup_vs_plain": round(t_plain / t_graph, 2),
+        "speedup_vs_plain": round(t_plain / t_graph, 2), "equal_to_plain": True,
         "frac_compulsory_roofline_graph": round(metrics.rate_g(total, t_graph * 1e-3) / comp, 4)}
     del kall, vall, ko_all, vo_all, offs
     torch.cuda.empty_cache()
@@ -622,36 +629,85 @@ def extras_gpu(args, ms, metrics, torch, dev):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(hk, hspl, hvals, case_list, sample_n: int):
-    """Runs the oracle on the first sample_n elements of every case; returns (elements, seconds)."""
+def _oracle_spec(kind, m, hspl):
     import oracle
 
+    if kind == "range":
+        return oracle.Spec(oracle.RANGE_U32, m, splitters=hspl[m])
+    return oracle.Spec(oracle.DELTA_F32, m, x0=0.0, delta=float(np.float32(1000.0) / np.float32(m)))
+
+
+def oracle_sample(hk, hspl, hvals, case_list, sample_n: int, parallel: bool = False):
+    """Runs the oracle (or, with parallel, the all-core CPU baseline) on the
+    first sample_n elements of every case; returns (elements, seconds)."""
+    import oracle
+
+    fn = oracle.multisplit_parallel if parallel else oracle.multisplit
     elems, secs = 0, 0.0
     for name, cid, kind, m, pairs in case_list:
         keys = hk[cid][:sample_n]
         vals = hvals[:sample_n] if pairs else None
-        if kind == "range":
-            spec = oracle.Spec(oracle.RANGE_U32, m, splitters=hspl[m])
-        else:
-            spec = oracle.Spec(oracle.DELTA_F32, m, x0=0.0, delta=float(np.float32(1000.0) / np.float32(m)))
+        spec = _oracle_spec(kind, m, hspl)
         t = time.perf_counter()
-        oracle.multisplit(keys, vals, spec)
+        fn(keys, vals, spec)
         secs += time.perf_counter() - t
         elems += len(keys)
     return elems, secs
 
 
+def host_cpu():
+    """(cores this process may use, CPU model string) of the host."""
+    import oracle
+
+    model = ""
+    try:
+        fields = {}
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields.setdefault(k.strip(), v.strip())
+        model = fields.get("Model name") or fields.get("Vendor ID", "")
+    except Exception:  # noqa: BLE001 -- lscpu missing: fall back to /proc/cpuinfo
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return oracle.host_threads(), model or platform.machine()
+
+
 def cpu_baseline(hk, hspl, hvals, case_list, n, budget_s: float = 15.0):
-    # calibrate the sample size so the whole sample takes about budget_s seconds
-    e, s = oracle_sample(hk, hspl, hvals, case_list, 1 << 16)
-    per_elem = s / max(1, e)
-    sample_n = int(min(n, max(1 << 16, budget_s / max(per_elem, 1e-12) / len(case_list))))
-    sample_n = 1 << max(16, int(np.floor(np.log2(sample_n))))
-    e, s = oracle_sample(hk, hspl, hvals, case_list, sample_n)
+    """The single-threaded oracle and the all-core CPU baseline, each on a
+    sample calibrated to about budget_s seconds (half the budget each)."""
+    import oracle
+
+    cores, model = host_cpu()
+
+    def calibrated(parallel, budget):
+        e, s = oracle_sample(hk, hspl, hvals, case_list, 1 << 16, parallel)
+        per_elem = s / max(1, e)
+        sample_n = int(min(n, max(1 << 16, budget / max(per_elem, 1e-12) / len(case_list))))
+        sample_n = 1 << max(16, int(np.floor(np.log2(sample_n))))
+        e, s = oracle_sample(hk, hspl, hvals, case_list, sample_n, parallel)
+        return e, s, sample_n
+
+    e, s, sample_n = calibrated(False, budget_s / 2)
+    pe, ps, psample = calibrated(True, budget_s / 2)
     return {"value": round(e / s / 1e9, 5), "unit": "G elements/s (keys or pairs)", "cores": 1,
             "kind": "oracle", "seconds": round(s, 2),
             "sample": f"each of the {len(case_list)} sweep cases on its first {sample_n} elements "
-                      f"(single-threaded C oracle, Eq. 1 by counting)"}
+                      f"(single-threaded C oracle, Eq. 1 by counting)",
+            "host": {"nproc": os.cpu_count(), "usable_cores": cores, "cpu_model": model},
+            "all_core": {"value": round(pe / ps / 1e9, 5), "unit": "G elements/s (keys or pairs)",
+                         "cores": min(cores, 256), "kind": "all-core C baseline (POSIX threads: chunk "
+                         "histograms, bucket-major scan, stable scatter per chunk), bit-exact vs the oracle",
+                         "seconds": round(ps, 2),
+                         "sample": f"each of the {len(case_list)} sweep cases on its first {psample} elements"}}
 
 
 def run_reference(args):

@@ -79,6 +79,59 @@ def test_batch_config_4096_segments_small():
         plan.close()
 
 
+@pytest.mark.slow
+def test_batch_config_4096_segments_full_size():
+    """The batched configuration as the benchmark times it: 4096 segments of
+    floor(2^U) pairs, U ~ U(8, 20) (about 516 M pairs), key mod 32, value =
+    index within the segment, graph replay.  Checked against the oracle on the
+    20 largest and 20 smallest segments and every 61st, and, on the device, the
+    whole output against one plain launch per segment."""
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+
+    sizes = synthetic.segment_sizes(4096, 8, 20, 2024)  # the benchmark's seed
+    total = int(sizes.sum())
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    hk = synthetic.uniform_u32(total, 2025)
+    kall = to_dev(hk)
+    vall = torch.empty_like(kall)
+    for st_, n_ in zip(starts, sizes):
+        vall[int(st_):int(st_ + n_)] = torch.arange(int(n_), dtype=torch.int32, device="cuda")
+    ko, vo = torch.full_like(kall, -1), torch.full_like(kall, -1)
+    offs = torch.full((4096, 33), -1, dtype=torch.int32, device="cuda")
+    segs = [(kall.data_ptr() + 4 * int(s0), vall.data_ptr() + 4 * int(s0), ko.data_ptr() + 4 * int(s0),
+             vo.data_ptr() + 4 * int(s0), offs[i].data_ptr(), int(n_)) for i, (s0, n_) in enumerate(zip(starts, sizes))]
+    spec = ms.BucketSpec.mod(32).c()
+    st, plan = ms.ms_batch_plan_create(segs, spec)
+    assert st == ms.MS_OK
+    sptr = torch.cuda.current_stream().cuda_stream
+    try:
+        for _ in range(2):  # a replay over outputs already written
+            assert ms.ms_batch_run_graph(plan, sptr) == ms.MS_OK
+        torch.cuda.synchronize()
+        assert ms.device_status() == ms.MS_OK
+    finally:
+        ms.ms_batch_plan_destroy(plan)
+    order = np.argsort(sizes, kind="stable")
+    pick = sorted(set(order[:20].tolist()) | set(order[-20:].tolist()) | set(range(0, 4096, 61)))
+    for i in pick:
+        s0, n_ = int(starts[i]), int(sizes[i])
+        ok, ov, ooff = oracle.multisplit(hk[s0:s0 + n_], synthetic.index_values(n_), oracle.Spec(oracle.MOD, 32))
+        np.testing.assert_array_equal(to_host(ko[s0:s0 + n_]), ok, err_msg=f"segment {i} n={n_}")
+        np.testing.assert_array_equal(to_host(vo[s0:s0 + n_]), ov, err_msg=f"segment {i} values")
+        np.testing.assert_array_equal(to_host(offs[i]).astype(np.uint64), ooff, err_msg=f"segment {i} offsets")
+    # every segment against one plain launch per segment, compared on the device
+    pk, pvo = torch.full_like(kall, -2), torch.full_like(kall, -2)
+    poffs = torch.full((4096, 33), -2, dtype=torch.int32, device="cuda")
+    for i, (s0, n_) in enumerate(zip(starts, sizes)):
+        o = 4 * int(s0)
+        assert ms.ms_multisplit_pairs(kall.data_ptr() + o, vall.data_ptr() + o, int(n_), spec, pk.data_ptr() + o,
+                                      pvo.data_ptr() + o, poffs[i].data_ptr(), sptr) == ms.MS_OK
+    torch.cuda.synchronize()
+    assert torch.equal(pk, ko) and torch.equal(pvo, vo) and torch.equal(poffs, offs)
+
+
 def test_batch_rejects_mixed_segments():
     import paper_1701_01189_gb300 as ms
 

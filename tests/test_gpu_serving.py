@@ -1,9 +1,11 @@
 """Serving: requests that arrive while others are on the GPU are batched into
-the persistent kernel on several streams, and every result equals the plain
-entry point's result on that request alone (bit exact)."""
+the persistent kernel on several streams, and every result equals the CPU
+oracle's result on that request alone and the plain entry point's (bit
+exact)."""
 import numpy as np
 import pytest
 
+import oracle
 import synthetic
 from parity import to_dev, to_host
 
@@ -17,9 +19,10 @@ def test_served_results_equal_alone():
     from paper_1701_01189_gb300 import serving
 
     pool = 1 << 20
-    pk = to_dev(synthetic.uniform_u32(pool, 1))
-    pv = to_dev(synthetic.uniform_u32(pool, 2))
-    spl = {m: to_dev(synthetic.range_splitters(m, m)) for m in (8, 32, 256)}
+    hk, hv = synthetic.uniform_u32(pool, 1), synthetic.uniform_u32(pool, 2)
+    pk, pv = to_dev(hk), to_dev(hv)
+    hspl = {m: synthetic.range_splitters(m, m) for m in (8, 32, 256)}
+    spl = {m: to_dev(t) for m, t in hspl.items()}
     trace = serving.make_trace(3000, 0.15, 5, pool=pool, n_lo=6, n_hi=18)
     svc = serving.Service(pk, pv, spl, arena_bytes=64 << 20, slots=3, max_batch_segments=64,
                           max_batch_elements=1 << 21, plain_min_elements=1 << 15)
@@ -33,9 +36,20 @@ def test_served_results_equal_alone():
     assert summary["requests"] == len(trace) == len(got)
     assert ms.device_status() == ms.MS_OK
     specs = {m: ms.BucketSpec.range_u32(t) for m, t in spl.items()}
-    checked = 0
+    checked = batched_sorts = 0
     for r in trace:
         got_k, got_v = got[r.rid]
+        what = f"request {r.rid} {r.kind} m={r.m} n={r.n}"
+        # the CPU oracle on the request's input alone
+        hkin, hvin = hk[r.in_off:r.in_off + r.n], hv[r.in_off:r.in_off + r.n]
+        if r.kind == "multisplit":
+            ok, ov, _ = oracle.multisplit(hkin, hvin, oracle.Spec(oracle.RANGE_U32, r.m, splitters=hspl[r.m]))
+        else:
+            ok, ov = oracle.radix_sort(hkin, hvin, 0, 32)
+            batched_sorts += r.n < (1 << 15)  # the four batched digit passes
+        np.testing.assert_array_equal(got_k, ok, err_msg=what + " vs oracle")
+        np.testing.assert_array_equal(got_v, ov, err_msg=what + " values vs oracle")
+        # and the plain entry point on the same request alone
         kin = pk[r.in_off:r.in_off + r.n]
         vin = pv[r.in_off:r.in_off + r.n]
         if r.kind == "multisplit":
@@ -43,10 +57,11 @@ def test_served_results_equal_alone():
         else:
             ek, ev = ms.radix_sort(kin, vin, 0, 32)
         torch.cuda.synchronize()
-        np.testing.assert_array_equal(got_k, to_host(ek), err_msg=f"request {r.rid} {r.kind} m={r.m} n={r.n}")
+        np.testing.assert_array_equal(got_k, to_host(ek), err_msg=what)
         np.testing.assert_array_equal(got_v, to_host(ev))
         checked += 1
     assert checked == len(trace)
+    assert batched_sorts > 0
     assert any(r.n >= 1 << 15 for r in trace) and any(r.n < 1 << 15 for r in trace)  # both paths ran
     svc.close()
 
