@@ -17,6 +17,11 @@ package.  It shares no code with the CUDA library in
   different algorithm from the LSD multisplit passes it checks.
 
 Parity pins for each function live in ``tests/test_oracle_pins.py``.
+
+``multisplit_parallel`` is not part of the oracle: it is the all-core CPU
+baseline the benchmark times (``ms_cpu_parallel.c``: chunk histograms, a
+bucket-major scan, a stable scatter per chunk, on POSIX threads), checked bit
+for bit against ``multisplit`` in ``tests/test_cpu_parallel.py``.
 """
 from __future__ import annotations
 
@@ -30,6 +35,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ms_oracle.c")
+_PAR_SRC = os.path.join(_HERE, "ms_cpu_parallel.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS: dict = {}
@@ -74,6 +80,63 @@ def build(mutant: int = 0) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
     return out
+
+
+def build_parallel() -> str:
+    """Compile the all-core CPU baseline (ms_cpu_parallel.c)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "libms_cpu_parallel.so")
+    if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_PAR_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-pthread", "-shared", "-fPIC",
+               "-o", tmp, _PAR_SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+    return out
+
+
+_PAR = None
+
+
+def _par_lib():
+    global _PAR
+    with _LOCK:
+        if _PAR is None:
+            lib = ctypes.CDLL(build_parallel())
+            P = ctypes.c_void_p
+            lib.par_multisplit.argtypes = [P, P, ctypes.c_size_t, P, P, P, P, ctypes.c_int]
+            lib.par_multisplit.restype = ctypes.c_int
+            _PAR = lib
+        return _PAR
+
+
+def host_threads() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def multisplit_parallel(keys, vals, spec: Spec, threads: int | None = None):
+    """The all-core CPU baseline (not the oracle): same result as multisplit, m <= 256."""
+    keys = _u32(keys)
+    n = len(keys)
+    ko = np.empty(n, np.uint32)
+    vo = None
+    vptr = None
+    if vals is not None:
+        vals = _u32(vals)
+        vo = np.empty(n, np.uint32)
+        vptr = vals.ctypes.data
+    off = np.empty(spec.m + 1, np.uint64)
+    cs, _keep = _cspec(spec)
+    rc = _par_lib().par_multisplit(keys.ctypes.data, vptr, n, ctypes.byref(cs), ko.ctypes.data,
+                                   vo.ctypes.data if vo is not None else None, off.ctypes.data,
+                                   int(threads or host_threads()))
+    if rc != 0:
+        raise RuntimeError(f"par_multisplit failed ({rc})")
+    return ko, vo, off
 
 
 def _lib(mutant: int = 0):
