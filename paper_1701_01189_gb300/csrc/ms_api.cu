@@ -69,16 +69,6 @@ cudaError_t scratch_alloc(DeviceCtx& ctx, void** p, size_t bytes, cudaStream_t s
 
 cudaError_t scratch_free(void* p, cudaStream_t stream) { return p ? cudaFreeAsync(p, stream) : cudaSuccess; }
 
-__global__ void k_counts_from_offsets(const uint32_t* offsets, uint32_t* counts, uint32_t m) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < m) counts[b] = offsets[b + 1] - offsets[b];
-}
-
-cudaError_t launch_counts_from_offsets(const uint32_t* offsets, uint32_t* counts, uint32_t m, cudaStream_t s) {
-  k_counts_from_offsets<<<1, 256, 0, s>>>(offsets, counts, m);
-  return cudaGetLastError();
-}
-
 cudaError_t run_multisplit(const Call& c, DeviceCtx& ctx) {
   switch (c.kind) {
     case kRange: return run_multisplit_range(c, ctx);

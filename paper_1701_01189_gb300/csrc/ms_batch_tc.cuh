@@ -9,9 +9,9 @@
 // counts (one shared atomic per key, no ranks), and every CTA copies the next
 // item's tile into the other of two shared-memory slots with asynchronous
 // 4-byte copies (any alignment) while it works on the current one.  Items
-// are taken by ticket and the next ticket is taken before the current item is
-// done; a waiting post-scan item only waits for histogram items, whose
-// tickets are all smaller and whose holders never wait, so every wait ends.
+// are taken by ticket, three tickets ahead of the current item; a waiting
+// post-scan item only waits for histogram items, whose tickets are all
+// smaller and whose holders never wait, so every wait ends.
 #pragma once
 
 #include "ms_tc.cuh"
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
   constexpr uint32_t T = Lay::T;
   constexpr uint32_t SW = Lay::kSlotWords;
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_next, s_flag;
+  __shared__ uint32_t s_tk[4], s_flag;
   __shared__ uint32_t s_delta[kTcMaxM], s_start[kTcMaxM];
   __shared__ __align__(16) uint32_t s_warp[8];
   const DevSpec& sp = a.sp;
@@ -85,20 +85,37 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
     cp_async_commit();
   };
 
-  if (t == 0) s_next = atomicAdd(a.ticket, 1u);
+  // Tickets are taken three items ahead, and the descriptors of the later
+  // items are pulled into L1 in two steps (the item entry, then the segment
+  // it names) while the current item is worked on, so that the copy of the
+  // next item's tile starts without waiting on their loads.  (Holding
+  // unstarted tickets is safe: a CTA holds histogram tickets only while it
+  // works on a histogram item, which never waits.)
+  auto prefetch_l1 = [](const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); };
+  if (t == 0) {
+    s_tk[0] = atomicAdd(a.ticket, 1u);
+    s_tk[1] = atomicAdd(a.ticket, 1u);
+    s_tk[2] = atomicAdd(a.ticket, 1u);
+    for (int k = 1; k < 3; ++k)
+      if (s_tk[k] < n_items) prefetch_l1(a.items + 1 + s_tk[k]);
+  }
   __syncthreads();
-  uint32_t cur = s_next;
+  uint32_t cur = s_tk[0], nxt = s_tk[1], nxt2 = s_tk[2];
   uint32_t slot = 0;
   fetch(cur, 0);
 
   while (cur < n_items) {
-    __syncthreads();  // the other slot's last item is written out; everyone read s_next
-    if (t == 0) s_next = atomicAdd(a.ticket, 1u);
-    __syncthreads();
-    const uint32_t nxt = s_next;
+    __syncthreads();  // the other slot's last item is written out; everyone read s_tk[3]
+    if (t == 0) {
+      if (nxt2 < n_items) prefetch_l1(a.segs + a.items[1 + nxt2].x);  // its entry came in an item ago
+      const uint32_t nn = atomicAdd(a.ticket, 1u);
+      s_tk[3] = nn;
+      if (nn < n_items) prefetch_l1(a.items + 1 + nn);
+    }
     fetch(nxt, slot ^ 1u);
     cp_async_wait<1>();  // this thread's copies of the current item landed
     __syncthreads();     // everyone's
+    const uint32_t nn = s_tk[3];
 
     const uint2 item = a.items[1 + cur];
     const uint32_t seg = item.x, tile = item.y;
@@ -282,6 +299,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
       }
     }
     cur = nxt;
+    nxt = nxt2;
+    nxt2 = nn;
     slot ^= 1u;
   }
   cp_async_wait<0>();  // nothing may be in flight into shared memory at exit

@@ -91,6 +91,84 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return wpre + x - v;
 }
 
+// Eq. 2 for chunk c from the chunk-major histograms H[c' * mp + b] (rows of
+// mp words, mp a power of two with m <= mp <= 32 and 4 <= mp, zero beyond m):
+// end[b] = (keys of buckets < b) + (keys of bucket b in chunks c' <= c), the
+// end of bucket b's share of chunk c in the output; CTA 0 also writes the
+// m + 1 bucket starts.  The first 256 threads read H as 16-byte vectors (a
+// vector is 4 buckets of one chunk; consecutive threads, consecutive
+// vectors), so a thread always sums the same 4 buckets; the sums are reduced
+// over the lanes, then over the warps, and warp 0 scans the bucket totals.
+// All threads of the block (>= 256) call it; s_scr: 2 * 8 * 32 words of
+// scratch (end: m words).  Ends with a block barrier.
+__device__ __forceinline__ void chunk_offsets(const uint32_t* H, uint32_t G, uint32_t m, uint32_t mp, uint32_t c,
+                                              uint32_t* end, uint32_t* s_scr, uint32_t* offsets) {
+  const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
+  const uint32_t q = mp >> 2;                        // vectors per row: 1, 2, 4 or 8
+  const uint32_t lq = q >= 8u ? 3u : q >= 4u ? 2u : q >= 2u ? 1u : 0u;
+  const uint32_t b0 = (t & (q - 1u)) << 2;           // this thread's buckets b0 .. b0 + 3
+  uint32_t inc[4] = {0u, 0u, 0u, 0u}, all[4] = {0u, 0u, 0u, 0u};
+  if (t < 256u) {
+    const uint32_t nvec = G * q;
+    const uint4* hv = reinterpret_cast<const uint4*>(H);
+#pragma unroll 16
+    for (uint32_t i = t; i < nvec; i += 256u) {
+      const uint4 v = __ldcg(hv + i);
+      const bool le = (i >> lq) <= c;
+      all[0] += v.x;
+      all[1] += v.y;
+      all[2] += v.z;
+      all[3] += v.w;
+      inc[0] += le ? v.x : 0u;
+      inc[1] += le ? v.y : 0u;
+      inc[2] += le ? v.z : 0u;
+      inc[3] += le ? v.w : 0u;
+    }
+  }
+  // lanes equal modulo q hold the same buckets
+#pragma unroll
+  for (uint32_t d = 16u; d > 0u; d >>= 1) {
+    if (d >= q) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        all[k] += __shfl_xor_sync(kFull, all[k], d);
+        inc[k] += __shfl_xor_sync(kFull, inc[k], d);
+      }
+    }
+  }
+  if (t < 256u && lane < q) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      s_scr[w * 32u + b0 + k] = inc[k];
+      s_scr[256u + w * 32u + b0 + k] = all[k];
+    }
+  }
+  __syncthreads();
+  if (t < 32u) {
+    uint32_t tot = 0, incs = 0;
+    if (t < mp) {
+#pragma unroll
+      for (uint32_t k = 0; k < 8u; ++k) {
+        incs += s_scr[k * 32u + t];
+        tot += s_scr[256u + k * 32u + t];
+      }
+    }
+    uint32_t x = tot;  // inclusive scan of the bucket totals over the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, d);
+      if (t >= (uint32_t)d) x += y;
+    }
+    const uint32_t start = x - tot;
+    if (t < m) end[t] = start + incs;
+    if (c == 0u && offsets != nullptr) {
+      if (t < m) offsets[t] = start;
+      if (t == m - 1u) offsets[m] = x;
+    }
+  }
+  __syncthreads();
+}
+
 // Programmatic dependent launch: a kernel lets the next one in the stream
 // start early (launch_dependents); the dependent kernel waits for the earlier
 // grid to complete, and its writes to be visible, before reading its results.

@@ -34,9 +34,6 @@ struct Call {
   uint32_t* counts;      // non-null: histogram only -- counts[b] for b < m, no permutation (ms_histogram)
 };
 
-// counts[b] = offsets[b+1] - offsets[b] for b < m (stream-ordered; ms_api.cu).
-cudaError_t launch_counts_from_offsets(const uint32_t* offsets, uint32_t* counts, uint32_t m, cudaStream_t s);
-
 // Kernel variant of one multisplit: post-scan tile shape (0: 8 warps x 16
 // keys, 1: 16 x 8, 2: 8 x 8), rank mode (kRankBallot only for m <= 8,
 // kRankTable) and whether the tile is reordered before the writes.

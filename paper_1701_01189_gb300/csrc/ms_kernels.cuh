@@ -45,7 +45,10 @@ struct PostscanArgs {
   uint32_t tiles_per_cta;
   uint32_t num_tiles;
   uint32_t G;
-  const uint32_t* Gx;  // exclusive scan of row-vectorised H (m*G entries)
+  const uint32_t* Gx;  // m <= 32: chunk-major histograms H[c * mp + b] (mp: 4, 8, 16 or 32 >= m); m > 32:
+                       // the exclusive scan of
+                       // the row-vectorised, bucket-major H (m*G entries)
+  uint32_t* offsets;   // m <= 32: the m + 1 bucket starts, written by CTA 0 (or nullptr)
   uint32_t* err;       // device status word
   uint32_t prefetch;   // 1: bulk-prefetch the next tiles into L2
   uint32_t reverse;    // 1: walk the chunk's tiles last to first
@@ -301,14 +304,26 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
   if (threadIdx.x == 0)
     for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);  // inputs are not written by the pre-scan
   build_bucket_tables<KIND, NB>(sp, s_tbl, s_lut);  // ends with a barrier
-  pdl_wait();  // H scanned by the pre-scan grid
+  pdl_wait();  // H complete (scanned, for m > 32)
   // next global position of each bucket: chunk start (forward) or chunk end (reverse)
-  const uint32_t len = m * a.G;
-  for (uint32_t b = threadIdx.x; b < m; b += THREADS) {
-    const uint32_t e = b * a.G + c;
-    s_run[b] = a.reverse ? ((e + 1 < len) ? a.Gx[e + 1] : a.n) : a.Gx[e];
+  if (m <= 32u) {
+    // Eq. 2 from the chunk histograms (rows of 4, 8, 16 or 32 words; the 512
+    // words from s_delta on -- s_delta, s_warp, the start of s_cnt -- as
+    // scratch: each is written before it is read again)
+    const uint32_t mp = m <= 4u ? 4u : m <= 8u ? 8u : m <= 16u ? 16u : 32u;
+    chunk_offsets(a.Gx, a.G, m, mp, c, s_run, s_delta, a.offsets);
+    if (!a.reverse) {
+      for (uint32_t b = threadIdx.x; b < m; b += THREADS) s_run[b] -= __ldcg(a.Gx + (size_t)c * mp + b);
+      __syncthreads();
+    }
+  } else {
+    const uint32_t len = m * a.G;
+    for (uint32_t b = threadIdx.x; b < m; b += THREADS) {
+      const uint32_t e = b * a.G + c;
+      s_run[b] = a.reverse ? ((e + 1 < len) ? a.Gx[e + 1] : a.n) : a.Gx[e];
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   uint32_t* wc = s_cnt + w * S;
   uint32_t* wpeer = s_peer + w * 2 * m_pad;

@@ -55,7 +55,9 @@ struct RadixHistArgs {
 
 // Digit histograms of every pass in one read of the keys.  Per warp, 32-bit
 // counters [pass][digit] in shared memory; at the end the CTA adds its counts
-// into the global histograms.
+// into the global histograms.  The passes (at most four) are unrolled with
+// their shifts and masks kept in registers: the kernel is bound by its
+// instruction issue, not by the bytes it reads.
 __global__ void __launch_bounds__(kHistNW * 32) k_radix_hist(RadixHistArgs a) {
   constexpr uint32_t T = kHistNW * 32 * kHistItems;
   extern __shared__ __align__(16) uint32_t smem[];
@@ -63,20 +65,27 @@ __global__ void __launch_bounds__(kHistNW * 32) k_radix_hist(RadixHistArgs a) {
   uint32_t* wh = smem + w * 4 * 256;
   for (uint32_t i = threadIdx.x; i < kHistNW * 4 * 256; i += kHistNW * 32) smem[i] = 0u;
   __syncthreads();
+  uint32_t sh[4], mk[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    sh[p] = a.begin_bit + 8u * p;
+    const uint32_t bits = (uint32_t)p < a.passes ? min(8u, a.end_bit - sh[p]) : 0u;
+    mk[p] = (1u << bits) - 1u;
+    sh[p] = min(sh[p], 31u);
+  }
+  const uint32_t passes = a.passes;
   for (size_t tb = (size_t)blockIdx.x * T; tb < a.n; tb += (size_t)gridDim.x * T) {
     const uint32_t rem = (uint32_t)min((size_t)T, (size_t)a.n - tb);
     const uint32_t off0 = w * (32 * kHistItems) + lane;
     uint32_t key[kHistItems];
 #pragma unroll
-    for (int i = 0; i < kHistItems; ++i) key[i] = (off0 + i * 32 < rem) ? a.keys[tb + off0 + i * 32] : 0u;
+    for (int i = 0; i < kHistItems; ++i) key[i] = (off0 + i * 32 < rem) ? __ldcs(a.keys + tb + off0 + i * 32) : 0u;
 #pragma unroll
     for (int i = 0; i < kHistItems; ++i) {
       if (off0 + i * 32 < rem) {
-        for (uint32_t p = 0; p < a.passes; ++p) {
-          const uint32_t sh = a.begin_bit + 8 * p;
-          const uint32_t bits = min(8u, a.end_bit - sh);
-          atomicAdd(wh + p * 256 + ((key[i] >> sh) & ((1u << bits) - 1u)), 1u);
-        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+          if ((uint32_t)p < passes) atomicAdd(wh + p * 256 + ((key[i] >> sh[p]) & mk[p]), 1u);
       }
     }
   }

@@ -80,17 +80,17 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   const uint32_t post_k = ch.K * (kTcTile / T);
   const uint32_t post_l = (uint32_t)(((uint64_t)c.n + T - 1) / T);
   const uint32_t m = c.sp.m;
-  // Up to 32 buckets the last pre-scan CTA scans H (a few rounds); beyond,
-  // H is longer and the separate look-back scan does it in parallel tiles.
-  const bool fused = m <= kTcMaxM;
-  const uint32_t len = m * ch.G;
-  const uint32_t nscan = fused ? 0u : (len + kScanTile - 1) / kScanTile;
+  // Up to 32 buckets every post-scan CTA reads the chunk-major H whole and
+  // reduces its own offsets; beyond, H is longer and the look-back scan turns
+  // the bucket-major H into the offsets in parallel tiles.
+  const bool small = m <= kTcMaxM;
+  const uint32_t len = (small ? tc_rows(m) : m) * ch.G;  // small: chunk-major rows of tc_rows(m) words
+  const uint32_t nscan = small ? 0u : (len + kScanTile - 1) / kScanTile;
 
-  // scratch: H (m * G words, 16-byte aligned) | scan status (nscan u64) |
-  // arrival counter or ticket | (histogram only) offsets
+  // scratch: H (m * G words, 16-byte aligned) | scan status (nscan u64) | ticket
   const size_t h_bytes = ((size_t)len * 4 + 15) & ~(size_t)15;
   const size_t st_bytes = (size_t)nscan * 8;
-  const size_t bytes = h_bytes + st_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
+  const size_t bytes = h_bytes + st_bytes + 16;
   void* ws = nullptr;
   cudaError_t e = cudaSuccess;
   if (c.ws_fixed != nullptr) {
@@ -103,28 +103,23 @@ static cudaError_t run_ms_cfg(const Call& c, DeviceCtx& ctx) {
   uint32_t* H = static_cast<uint32_t*>(ws);
   auto* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + h_bytes);
   uint32_t* ticket = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes);
-  e = cudaMemsetAsync(ws, 0, h_bytes + st_bytes + 16, c.stream);  // H (the pre-scan adds into it), status, counter
+  e = cudaMemsetAsync(ws, 0, h_bytes + st_bytes + 16, c.stream);  // H (the pre-scan adds into it), status, ticket
 
   const uint32_t aligned =
       ((reinterpret_cast<uintptr_t>(c.keys_in) | reinterpret_cast<uintptr_t>(c.vals_in)) & 15u) == 0;
   const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
-  uint32_t* offsets = c.offsets;
-  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + st_bytes + 16);
   if (e == cudaSuccess) {
-    e = launch_prescan<KIND>(c, ctx, ch, H, fused, ticket, offsets);
+    e = launch_prescan<KIND>(c, ctx, ch, H, small ? 1u : ch.G, small ? tc_rows(m) : 1u, nullptr);
     trace_mark(slot, 1, c.stream);
   }
-  if (e == cudaSuccess && !fused) {
-    ScanArgs sa{H, len, ch.G, offsets, m, status, ticket, ctx.d_err};
+  if (e == cudaSuccess && !small) {
+    ScanArgs sa{H, len, ch.G, c.offsets, m, status, ticket, ctx.d_err};
     e = launch_scan_lookback(sa, c.stream);
   }
   trace_mark(slot, 2, c.stream);
-  if (e == cudaSuccess && c.counts != nullptr) {
-    e = launch_counts_from_offsets(offsets, c.counts, m, c.stream);
-    trace_mark(slot, 3, c.stream);
-  } else if (e == cudaSuccess) {
-    PostscanArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, c.sp, post_k, post_l, ch.G, H, ctx.d_err,
-                    aligned, 1u};
+  if (e == cudaSuccess) {
+    PostscanArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, c.sp, post_k, post_l, ch.G, H,
+                    small ? c.offsets : nullptr, ctx.d_err, aligned, 1u};
     // stage timing records events between the kernels: then a plain launch
     e = launch_dependent(kpost, ch.G, THREADS, smem_post, c.stream, slot >= 0, qa);
     trace_mark(slot, 3, c.stream);
@@ -161,6 +156,7 @@ static cudaError_t run_ms_ballot(const Call& c, DeviceCtx& ctx, const Variant& v
 // any m).
 template <int KIND>
 static cudaError_t run_ms_kind(const Call& c, DeviceCtx& ctx) {
+  if (c.counts != nullptr) return run_histogram<KIND>(c, ctx);
   const Variant v = choose_variant(c);
   if (v.rank == kRankThread && c.sp.m <= kTcMaxM) return run_tc<KIND>(c, ctx, v.shape);
   if (v.rank == kRankVote) return run_ms_pairs<KIND, 8, kRankVote, 1>(c, ctx, v.shape);

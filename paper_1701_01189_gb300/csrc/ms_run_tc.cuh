@@ -74,11 +74,11 @@ constexpr size_t kTcL2KeepBytes = (size_t)64 << 20;
 
 // The pre-scan of every design: `k_prescan_tc` (ms_tc.cuh) counting in
 // registers (m <= 8), per-thread counters (m <= 32) or per-lane byte counters
-// (m <= 256); if `fused`, its last CTA scans H and writes the offsets.
-// Chunks are whole 4096-key tiles.
+// (m <= 256), into H (strides hsb, hsc; nullptr: none) and/or the bucket
+// totals `tot`.  Chunks are whole 4096-key tiles.
 template <int KIND>
-static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking& ch, uint32_t* H, bool fused,
-                                  uint32_t* arrive, uint32_t* offsets) {
+static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking& ch, uint32_t* H, uint32_t hsb,
+                                  uint32_t hsc, uint32_t* tot) {
   const uint32_t m = c.sp.m;
   const int mode = m <= 8 ? kCountReg : m <= 32 ? kCountThread : kCountLaneBytes;
   // splitter lookup tables: 1024 cells x 8 copies (m <= 32), 4096 cells x 1 copy beyond
@@ -88,17 +88,14 @@ static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking&
   const bool vec = ((reinterpret_cast<uintptr_t>(c.keys_in)) & 15u) == 0;
   const size_t keep_tiles = kTcL2KeepBytes / ((size_t)kTcTile * 4);
   const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
-  TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, 1u, ch.K - keep, vec ? 1u : 0u, H, fused ? 1u : 0u, arrive,
-               offsets, lb, lw, c.sp};
+  TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, hsb, hsc, tot, lb, lw, c.sp};
   static LaunchInfo li[3];
-  // enough CTAs to fill the SMs: a chunk (one post-scan CTA's work) is split
-  // into `sub` runs of tiles when the post-scan has fewer CTAs than the
-  // pre-scan can keep resident
+  // one CTA per chunk, or, when the chunks outnumber the CTAs the SMs hold at
+  // once, one wave of those CTAs, each an equal run of tiles
   auto launch = [&](auto k, size_t smem, size_t smem_max, LaunchInfo& info) {
     const int resident = setup_kernel(info, k, kTcThreads, smem_max, smem, ctx.device);
-    const uint32_t want = (uint32_t)(ctx.sm_count * resident);
-    pa.sub = std::max(1u, std::min(ch.K, want / ch.G));  // one wave: a partial second wave only adds a tail
-    k<<<ch.G * pa.sub, kTcThreads, smem, c.stream>>>(pa);
+    const uint32_t grid = std::max(1u, std::min(ch.G, (uint32_t)(ctx.sm_count * resident)));
+    k<<<grid, kTcThreads, smem, c.stream>>>(pa);
   };
   if (mode == kCountLaneBytes)
     launch(k_prescan_tc<KIND, kCountLaneBytes>, tc_prescan_smem<KIND, kCountLaneBytes>(m, lb, lw),
@@ -112,11 +109,11 @@ static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking&
   return cudaGetLastError();
 }
 
-template <int KIND, bool PAIRS, int STAGES, int KPT>
+template <int KIND, bool PAIRS, int STAGES, int KPT, bool BULK>
 static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   constexpr uint32_t T = kTcThreads * KPT;  // post-scan tile; the pre-scan works in 4096-key tiles
-  auto kpost = k_postscan_tc<KIND, PAIRS, STAGES, KPT>;
-  using Lay = TcPostLayout<KIND, PAIRS, STAGES, KPT>;
+  auto kpost = k_postscan_tc<KIND, PAIRS, STAGES, KPT, BULK>;
+  using Lay = TcPostLayout<KIND, PAIRS, STAGES, KPT, BULK>;
   const DevSpec& sp = c.sp;
   // splitter lookup table of the post-scan: 512 cells x 4 copies (x 2 for
   // key-value pairs with more than 16 buckets, which keeps two CTAs per SM)
@@ -130,9 +127,9 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   const uint32_t post_k = ch.K * (kTcTile / T);
   const uint32_t post_l = (uint32_t)(((uint64_t)c.n + T - 1) / T);
   const uint32_t m = sp.m;
-  // scratch: H (m * G words) | arrival counter | (histogram only) offsets
-  const size_t h_bytes = ((size_t)m * ch.G * 4 + 15) & ~(size_t)15;
-  const size_t bytes = h_bytes + 16 + (c.counts != nullptr ? 4u * (m + 1) : 0u);
+  // scratch: H (chunk-major, rows of tc_rows(m) words; the pre-scan adds into it)
+  const size_t h_bytes = ((size_t)tc_rows(m) * ch.G * 4 + 15) & ~(size_t)15;
+  const size_t bytes = h_bytes;
   void* ws = nullptr;
   cudaError_t e = cudaSuccess;
   if (c.ws_fixed != nullptr) {
@@ -143,8 +140,7 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
     if (e != cudaSuccess) return e;
   }
   uint32_t* H = static_cast<uint32_t*>(ws);
-  uint32_t* arrive = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes);
-  e = cudaMemsetAsync(ws, 0, h_bytes + 16, c.stream);  // H (the pre-scan adds into it) and the counter
+  e = cudaMemsetAsync(ws, 0, h_bytes, c.stream);
 
   CUtensorMap tmk, tmv;
   std::memset(&tmk, 0, sizeof tmk);
@@ -153,18 +149,13 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   if (tma && PAIRS) tma = make_tile_map(&tmv, c.vals_in, c.n, T);
 
   const int slot = c.ws_fixed != nullptr ? -1 : trace_begin(c.stream);
-  uint32_t* offsets = c.offsets;
-  if (c.counts != nullptr) offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + h_bytes + 16);
   if (e == cudaSuccess) {
-    e = launch_prescan<KIND>(c, ctx, ch, H, true, arrive, offsets);
+    e = launch_prescan<KIND>(c, ctx, ch, H, 1u, tc_rows(m), nullptr);
     trace_mark(slot, 1, c.stream);
-    trace_mark(slot, 2, c.stream);  // the global scan runs inside the pre-scan
+    trace_mark(slot, 2, c.stream);  // the global scan is folded into the post-scan's set-up
   }
-  if (e == cudaSuccess && c.counts != nullptr) {
-    e = launch_counts_from_offsets(offsets, c.counts, m, c.stream);
-    trace_mark(slot, 3, c.stream);
-  } else if (e == cudaSuccess) {
-    TcPostArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, post_k, post_l, ch.G, H, ctx.d_err,
+  if (e == cudaSuccess) {
+    TcPostArgs qa{c.keys_in, c.vals_in, c.keys_out, c.vals_out, c.n, post_k, post_l, ch.G, H, c.offsets, ctx.d_err,
                   tma ? 1u : 0u, post_lb, post_lw, sp};
     // stage timing records events between the kernels: then a plain launch
     e = launch_dependent(kpost, ch.G, kTcThreads, smem_post, c.stream, slot >= 0, tmk, tmv, qa);
@@ -174,17 +165,38 @@ static cudaError_t run_tc_cfg(const Call& c, DeviceCtx& ctx) {
   return e != cudaSuccess ? e : e2;
 }
 
+// Device histogram (Section 7.3): the pre-scan alone, its CTAs adding their
+// counts into c.counts (zeroed first).  Any m <= 256.
+template <int KIND>
+static cudaError_t run_histogram(const Call& c, DeviceCtx& ctx) {
+  const Chunking ch = make_chunking(c.n, kTcTile, (uint32_t)(ctx.sm_count * 3));
+  cudaError_t e = cudaMemsetAsync(c.counts, 0, (size_t)c.sp.m * 4, c.stream);
+  const int slot = trace_begin(c.stream);
+  if (e == cudaSuccess) e = launch_prescan<KIND>(c, ctx, ch, nullptr, 0u, 0u, c.counts);
+  trace_mark(slot, 1, c.stream);
+  trace_mark(slot, 2, c.stream);
+  trace_mark(slot, 3, c.stream);
+  return e;
+}
+
 // Variant shape 2 selects 8 keys per thread, any other 16; shape 1 a
-// 3-slot ring for keys only (key-value pairs keep 2 slots).
+// 3-slot ring for keys only (key-value pairs keep 2 slots).  Up to
+// kTcBulkMaxM buckets the write-out goes by bulk copies per bucket run.
+template <int KIND, bool BULK>
+static cudaError_t run_tc_bulk(const Call& c, DeviceCtx& ctx, int shape) {
+  if (shape == 2) {
+    if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2, 8, BULK>(c, ctx);
+    return run_tc_cfg<KIND, false, 2, 8, BULK>(c, ctx);
+  }
+  if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2, 16, BULK>(c, ctx);
+  if (shape == 1) return run_tc_cfg<KIND, false, 3, 16, BULK>(c, ctx);
+  return run_tc_cfg<KIND, false, 2, 16, BULK>(c, ctx);
+}
+
 template <int KIND>
 static cudaError_t run_tc(const Call& c, DeviceCtx& ctx, int shape) {
-  if (shape == 2) {
-    if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2, 8>(c, ctx);
-    return run_tc_cfg<KIND, false, 2, 8>(c, ctx);
-  }
-  if (c.vals_in != nullptr) return run_tc_cfg<KIND, true, 2, 16>(c, ctx);
-  if (shape == 1) return run_tc_cfg<KIND, false, 3, 16>(c, ctx);
-  return run_tc_cfg<KIND, false, 2, 16>(c, ctx);
+  if (c.sp.m <= kTcBulkMaxM) return run_tc_bulk<KIND, true>(c, ctx, shape);
+  return run_tc_bulk<KIND, false>(c, ctx, shape);
 }
 
 }  // namespace ms

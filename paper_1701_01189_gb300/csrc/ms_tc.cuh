@@ -28,10 +28,13 @@
 // so a thread's 64 contiguous bytes are read with four conflict-free 16-byte
 // loads.  The pre-scan reads the keys straight into registers with 16-byte
 // loads, keeping the last part of every chunk in L2 (evict_last) for the
-// post-scan, which walks its chunk last tile first.  The last pre-scan CTA to
-// finish computes the global scan of H (Section 4.3, Eq. 2), so the
-// post-scan, launched as a programmatic dependent, starts its set-up and first
-// copies while the pre-scan drains.
+// post-scan, which walks its chunk last tile first.  The global scan of H
+// (Section 4.3, Eq. 2) is not a separate step: every post-scan CTA reads the
+// whole of H (m x G words, a few tens of KB from L2) and reduces the two terms
+// its chunk needs -- the keys of all smaller buckets and the keys of its
+// bucket in earlier chunks -- so no CTA scans H alone while the others wait.
+// The post-scan, launched as a programmatic dependent, starts its set-up and
+// first copies while the pre-scan drains.
 #pragma once
 
 #include <cuda.h>
@@ -47,6 +50,7 @@ constexpr int kTcKpt = 16;                         // keys per thread
 constexpr uint32_t kTcTile = kTcThreads * kTcKpt;  // 4096 keys = 128 rows of 32 words
 constexpr uint32_t kTcRow = 288;                   // words per bucket row: 256 counters + 4 pad words per 32
 constexpr uint32_t kTcMaxM = 32;
+constexpr uint32_t kTcBulkMaxM = 8;  // post-scan write-out by one bulk copy per bucket run up to this m
 
 // Counter rows (a power of two >= 4 and >= m): the scan covers R * 256 counters.
 __host__ __device__ constexpr uint32_t tc_rows(uint32_t m) { return m <= 4 ? 4u : m <= 8 ? 8u : m <= 16 ? 16u : 32u; }
@@ -176,23 +180,23 @@ __device__ __forceinline__ void tc_fixup(const uint32_t (&key)[N], uint32_t (&bk
 }
 
 // ---------------------------------------------------------------------------
-// Pre-scan: per-chunk bucket histograms (column c of H, bucket-major
-// H[b * G + c]), then (fused, m <= 32) in the last CTA to finish the exclusive
-// scan of the row-vectorised H in place and the bucket offsets.
+// Pre-scan: per-chunk bucket histograms, H[b * hsb + c * hsc] for bucket b
+// and chunk c -- bucket-major (hsb = G, hsc = 1) for the look-back scan of
+// m > 32, chunk-major (hsb = 1, hsc = m) for the post-scans of m <= 32, which
+// read H whole -- and, optionally, the bucket totals (the device histogram).
 struct TcPreArgs {
   const uint32_t* keys;
   uint32_t n;
   uint32_t tiles_per_chunk;  // K
   uint32_t num_tiles;        // L
   uint32_t G;                // chunks
-  uint32_t sub;              // CTAs per chunk (G * sub CTAs), each counting a run of the chunk's tiles
   uint32_t keep_from;        // chunk-relative tile index from which loads keep their lines in L2
+                             // (the grid: any number of CTAs, each an equal run of the tiles)
   uint32_t vec;              // keys 16-byte aligned
-  uint32_t* H;               // m * G words, bucket-major H[b * G + c], zero before the launch (the parts
-                             // of a chunk add their counts); the exclusive scan if fused
-  uint32_t fused;            // 1: the last CTA to finish scans H and writes the offsets
-  uint32_t* arrive;          // zero before the launch
-  uint32_t* offsets;         // m + 1 words, or nullptr
+  uint32_t* H;               // m * G words, zero before the launch (the parts of a chunk add their
+                             // counts), or nullptr
+  uint32_t hsb, hsc;         // strides of H: bucket, chunk
+  uint32_t* tot;             // m bucket totals, zero before the launch, or nullptr
   uint32_t lb, lw;           // lookup table: 2^lb cells, 2^lw copies (range buckets)
   DevSpec sp;
 };
@@ -217,8 +221,6 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
   constexpr int BB = MODE == kCountLaneBytes ? 8 : 5;  // bits of a bucket in the lookup table
   constexpr int NW = kTcThreads / 32;
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_warp[8];
-  __shared__ uint32_t s_last;
   const DevSpec& sp = a.sp;
   const uint32_t m = sp.m, R = tc_rows(m), m_pad = tc_mpad(m);
   const uint32_t cnt_words = MODE == kCountLaneBytes ? NW * m_pad * 9u : R * kTcRow;
@@ -235,15 +237,20 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
   uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // kCountThread/kCountReg: counter (bucket 0, thread t)
   uint32_t* wwords = s_cnt + w * m_pad * 8u;   // kCountLaneBytes: this warp's byte counters
   uint32_t* wtot = s_cnt + NW * m_pad * 8u + w * m_pad;  // ... and its 32-bit totals
-  // CTA (c, part): part `part` of the `sub` parts of chunk c
-  const uint32_t c = blockIdx.x / a.sub, part = blockIdx.x % a.sub;
-  const uint32_t c0 = c * a.tiles_per_chunk;  // first tile of the chunk
-  const uint32_t c1 = min(c0 + a.tiles_per_chunk, a.num_tiles);
-  const uint32_t per = (a.tiles_per_chunk + a.sub - 1) / a.sub;
-  const uint32_t t0 = min(c0 + part * per, c1);
-  const uint32_t t1 = min(t0 + per, c1);
+  // this CTA's share of the tiles: an equal run of them, cut at chunk
+  // boundaries, each piece's counts added into its chunk's column of H (so
+  // the grid is one wave whatever the number of chunks)
+  const uint32_t nct = gridDim.x;
+  const uint32_t K = a.tiles_per_chunk;
+  uint32_t ta, tz;
+  if (nct == a.G) {  // one CTA per chunk
+    ta = blockIdx.x * K;
+    tz = min(a.num_tiles, ta + K);
+  } else {
+    ta = (uint32_t)((uint64_t)a.num_tiles * blockIdx.x / nct);
+    tz = (uint32_t)((uint64_t)a.num_tiles * (blockIdx.x + 1u) / nct);
+  }
   const uint32_t nfull = a.n / kTcTile;  // tiles [0, nfull) are full
-  const uint32_t tv1 = a.vec ? max(t0, min(t1, nfull)) : t0;
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
 
   uint64_t creg = 0;       // kCountReg: eight 8-bit counters
@@ -282,9 +289,10 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
     for (int i = 0; i < 16; ++i) count1(bk[i]);
     since += 16u;
   };
-  // thread (w, lane) holds words w*512 + j*128 + 4*lane + e of the tile
+  // thread (w, lane) holds words w*512 + j*128 + 4*lane + e of the tile; the
+  // last tiles of every chunk keep their lines in L2 for the post-scan
   auto load16 = [&](uint32_t (&key)[16], uint32_t tile) {
-    const uint64_t pol = (tile - c0 >= a.keep_from) ? pol_last : pol_first;
+    const uint64_t pol = (tile % K >= a.keep_from) ? pol_last : pol_first;
     const uint32_t* src = a.keys + (size_t)tile * kTcTile + w * 512u + 4u * lane;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -295,97 +303,85 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
       key[4 * j + 3] = v.w;
     }
   };
+  auto put = [&](uint32_t b, uint32_t c, uint32_t cnt) {
+    if (cnt == 0u) return;
+    if (a.H != nullptr) atomicAdd(a.H + (size_t)b * a.hsb + (size_t)c * a.hsc, cnt);
+    if (a.tot != nullptr) atomicAdd(a.tot + b, cnt);
+  };
 
-  // full, aligned tiles: 16-byte loads, the next tile's loads in flight while
-  // this one is counted
-  if (t0 < tv1) {
-    uint32_t ka[16], kb[16];
-    load16(ka, t0);
-    for (uint32_t tile = t0; tile < tv1; tile += 2) {
-      if (tile + 1 < tv1) load16(kb, tile + 1);
-      count16(ka);
-      if (tile + 1 >= tv1) break;
-      if (tile + 2 < tv1) load16(ka, tile + 2);
-      count16(kb);
-    }
-  }
-  // the partial last tile, or every tile of an unaligned input (at most 16
-  // keys per thread per tile, so the byte counters are flushed per tile)
-  for (uint32_t tile = tv1; tile < t1; ++tile) {
-    const size_t tb = (size_t)tile * kTcTile;
-    const uint32_t rem = (uint32_t)min((size_t)kTcTile, (size_t)a.n - tb);
-    if constexpr (MODE != kCountThread)
-      if (since + 16u > 255u) flush();
-    for (uint32_t p = t; p < rem; p += kTcThreads) {
-      uint32_t flag = 0;
-      const uint32_t u = a.keys[tb + p];
-      uint32_t b = tc_bucket<KIND, BB>(u, sp, L, flag);
-      if constexpr (KIND == kRange)
-        if (flag & (1u << BB)) b = range_in_cell<BB>(u, L.word(u), s_tbl, m);
-      count1(b);
-    }
-    since += 16u;
-  }
-  if constexpr (MODE != kCountThread) flush();
-  __syncthreads();
-
-  if constexpr (MODE == kCountLaneBytes) {
-    // column c of H: the warps' totals summed per bucket
-    for (uint32_t b = t; b < m; b += kTcThreads) {
-      uint32_t s2 = 0;
-#pragma unroll
-      for (int ww = 0; ww < NW; ++ww) s2 += s_cnt[NW * m_pad * 8u + ww * m_pad + b];
-      if (s2) atomicAdd(a.H + (size_t)b * a.G + c, s2);
-    }
-  } else {
-    // column c of H: warp w sums buckets w, w+8, w+16, w+24 over the 256 threads
-    for (uint32_t b = w; b < m; b += kTcThreads / 32) {
-      const uint32_t* row = s_cnt + b * kTcRow + lane;
-      uint32_t s2 = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) s2 += row[36 * k];
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) s2 += __shfl_xor_sync(kFull, s2, d);
-      if (lane == 0 && s2) atomicAdd(a.H + (size_t)b * a.G + c, s2);
-    }
-  }
-  if (!a.fused) return;
-  __threadfence();
-  __syncthreads();
-  if (t == 0) s_last = (atomicAdd(a.arrive, 1u) == a.G * a.sub - 1u) ? 1u : 0u;
-  __syncthreads();
-  if (s_last == 0u) return;
-  __threadfence();
-
-  // Last CTA: exclusive scan of H_row in place (Eq. 2), bucket offsets, in
-  // rounds of 4096 entries (a few rounds for m <= 32; larger m take the
-  // separate look-back scan, see `fused`)
-  const uint32_t len = m * a.G;
-  uint32_t carry = 0;
-  for (uint32_t base = 0; base < len; base += kTcTile) {
-    uint32_t v[16];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const uint32_t idx = base + 16u * t + i;
-      v[i] = idx < len ? __ldcg(a.H + idx) : 0u;
-      sum += v[i];
-    }
-    uint32_t total;
-    uint32_t run = carry + tc_block_scan(sum, s_warp, &total);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const uint32_t idx = base + 16u * t + i;
-      if (idx < len) {
-        a.H[idx] = run;
-        if (a.offsets != nullptr && idx % a.G == 0u) a.offsets[idx / a.G] = run;
+  // counts tiles [t0, t1) of chunk c and adds them into its column of H
+  auto piece = [&](uint32_t c, uint32_t t0, uint32_t t1) {
+    const uint32_t tv1 = a.vec ? max(t0, min(t1, nfull)) : t0;
+    // full, aligned tiles: 16-byte loads, the next tile's loads in flight
+    // while this one is counted
+    if (t0 < tv1) {
+      uint32_t ka[16], kb[16];
+      load16(ka, t0);
+      for (uint32_t tile = t0; tile < tv1; tile += 2) {
+        if (tile + 1 < tv1) load16(kb, tile + 1);
+        count16(ka);
+        if (tile + 1 >= tv1) break;
+        if (tile + 2 < tv1) load16(ka, tile + 2);
+        count16(kb);
       }
-      run += v[i];
     }
-    carry += total;
-    __syncthreads();  // s_warp is rewritten by the next round
+    // the partial last tile, or every tile of an unaligned input (at most 16
+    // keys per thread per tile, so the byte counters are flushed per tile)
+    for (uint32_t tile = tv1; tile < t1; ++tile) {
+      const size_t tb = (size_t)tile * kTcTile;
+      const uint32_t rem = (uint32_t)min((size_t)kTcTile, (size_t)a.n - tb);
+      if constexpr (MODE != kCountThread)
+        if (since + 16u > 255u) flush();
+      for (uint32_t p = t; p < rem; p += kTcThreads) {
+        uint32_t flag = 0;
+        const uint32_t u = a.keys[tb + p];
+        uint32_t b = tc_bucket<KIND, BB>(u, sp, L, flag);
+        if constexpr (KIND == kRange)
+          if (flag & (1u << BB)) b = range_in_cell<BB>(u, L.word(u), s_tbl, m);
+        count1(b);
+      }
+      since += 16u;
+    }
+    if constexpr (MODE != kCountThread) flush();
+    __syncthreads();
+
+    // column c of H: the counts of this piece
+    if constexpr (MODE == kCountLaneBytes) {
+      for (uint32_t b = t; b < m; b += kTcThreads) {
+        uint32_t s2 = 0;
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) s2 += s_cnt[NW * m_pad * 8u + ww * m_pad + b];
+        put(b, c, s2);
+      }
+    } else {
+      // warp w sums buckets w, w+8, w+16, w+24 over the 256 threads
+      for (uint32_t b = w; b < m; b += kTcThreads / 32) {
+        const uint32_t* row = s_cnt + b * kTcRow + lane;
+        uint32_t s2 = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s2 += row[36 * k];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s2 += __shfl_xor_sync(kFull, s2, d);
+        if (lane == 0) put(b, c, s2);
+      }
+    }
+  };
+
+  if (nct == a.G) {
+    piece(blockIdx.x, ta, tz);  // one chunk
+  } else {
+    for (uint32_t t0 = ta; t0 < tz;) {
+      const uint32_t c = t0 / K;  // the chunk of this piece
+      const uint32_t t1 = min(tz, (c + 1u) * K);
+      piece(c, t0, t1);
+      t0 = t1;
+      if (t0 < tz) {  // counters cleared for the next piece
+        __syncthreads();
+        for (uint32_t i = t; i < cnt_words; i += kTcThreads) s_cnt[i] = 0u;
+        __syncthreads();
+      }
+    }
   }
-  if (t == 0 && a.offsets != nullptr) a.offsets[m] = carry;
 }
 
 // ---------------------------------------------------------------------------
@@ -399,52 +395,99 @@ struct TcPostArgs {
   uint32_t tiles_per_cta;
   uint32_t num_tiles;
   uint32_t G;
-  const uint32_t* Gx;  // exclusive scan of row-vectorised H (m * G entries)
+  const uint32_t* H;   // chunk histograms, chunk-major H[c * R + b] (G * R words, R = tc_rows(m))
+  uint32_t* offsets;   // m + 1 bucket starts (written by CTA 0), or nullptr
   uint32_t* err;       // device status word
   uint32_t tma;        // 1: full tiles arrive by tensor copies (inputs 16-byte aligned)
   uint32_t lb, lw;     // lookup table: 2^lb cells, 2^lw copies (range buckets)
   DevSpec sp;
 };
 
-// Dynamic shared memory (words), from a 1024-byte-aligned base: ring of
-// STAGES key slots (and value slots), counters R * 288, bucket bytes (T),
-// splitter table (32), lookup table.  1 KB of slack for the alignment.
-template <int KIND, bool PAIRS, int STAGES, int KPT>
+// Dynamic shared memory (words), from a 1024-byte-aligned base: a ring of
+// STAGES slots, each holding a tile's keys in T + 256 words (then its values
+// in as many, for pairs; 256 spare words keep every part 1024-byte aligned for
+// the swizzled tensor copies and give the reordered tile room for the
+// per-bucket padding below); counters R * 288; splitter table (32); lookup
+// table.  1 KB of slack for the alignment.
+template <int KIND, bool PAIRS, int STAGES, int KPT, bool BULK>
 struct TcPostLayout {
   static constexpr uint32_t T = kTcThreads * KPT;
-  static constexpr uint32_t kRingWords = STAGES * T * (PAIRS ? 2 : 1);
-  static __host__ __device__ uint32_t cnt() { return kRingWords; }
-  static __host__ __device__ uint32_t bkt(uint32_t R) { return cnt() + R * kTcRow; }
-  static __host__ __device__ uint32_t tbl(uint32_t R) { return bkt(R) + T / 4; }
-  static __host__ __device__ uint32_t lut(uint32_t R) { return tbl(R) + 32; }
+  // words of one array (keys or values) in a slot: 256 spare words for the
+  // padded runs of the bulk write-out, none otherwise
+  static constexpr uint32_t kPart = T + (BULK ? 256u : 0u);
+  static constexpr uint32_t kSlotWords = kPart * (PAIRS ? 2u : 1u);
+  // a bucket byte per reordered position for the write-out without bulk
+  // copies, unless the identifier is cheap to evaluate again
+  static constexpr bool kBytes = !BULK && !cheap_bucket<KIND>();
+  static __host__ __device__ uint32_t cnt(uint32_t) { return STAGES * kSlotWords; }
+  static __host__ __device__ uint32_t bkt(uint32_t m) { return cnt(m) + tc_rows(m) * kTcRow; }
+  static __host__ __device__ uint32_t tbl(uint32_t m) { return bkt(m) + (kBytes ? T / 4 : 0u); }
+  static __host__ __device__ uint32_t lut(uint32_t m) { return tbl(m) + 32; }
   static __host__ size_t bytes(uint32_t m, uint32_t lb, uint32_t lw) {
-    return 1024u + 4u * (size_t)(lut(tc_rows(m)) + tc_lut_words(KIND, lb, lw));
+    return 1024u + 4u * (size_t)(lut(m) + tc_lut_words(KIND, lb, lw));
   }
 };
 
+// Bucket of u for the post-scan.  Range buckets: a key of a flagged cell gets
+// a value >= 32 (the flag bit stays in the sum) that tc_fix_marked replaces
+// by the search; every other key gets its bucket (< 32), so the flagged keys
+// are found without reading the table again.
+template <int KIND>
+__device__ __forceinline__ uint32_t tc_bucket_marked(uint32_t u, const DevSpec& sp, const TcLut& L) {
+  if constexpr (KIND == kRange) {
+    const uint32_t e = L.word(u);
+    return (e & 63u) + ((u & L.fmask) >= (e >> 6) ? 1u : 0u);
+  } else {
+    return bucket_of<KIND, 5>(u, sp, nullptr, nullptr);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void tc_fix_marked(const uint32_t (&key)[N], uint32_t (&bk)[N], const uint32_t* tbl,
+                                              uint32_t m) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (bk[i] >= 32u) bk[i] = range_search<5>(key[i], tbl, m);
+}
+
 // KPT keys per thread (16, or 8: a 2048-key tile, half the registers per
 // thread, more CTAs per SM).
-template <int KIND, bool PAIRS, int STAGES, int KPT>
+//
+// Write-out.  BULK (up to kTcBulkMaxM buckets: runs of T/m keys or more) by
+// bulk copies: the tile is reordered in place in its slot with bucket b's run
+// placed at tile position + 4b + (delta_b mod 4), where delta_b = (the run's
+// first global position) - (its first tile position), so that every run sits
+// at the same address modulo 16 bytes in shared memory as in the output;
+// thread b then writes run b with one bulk copy (TMA) of its 16-byte-aligned
+// interior and at most three plain stores at each end -- the copy engine
+// reads shared memory and writes HBM without the load/store units.  A slot is
+// refilled only after its bulk copies have read it.  More buckets (short runs,
+// where a copy per run costs more than it saves): the tile is reordered in
+// place with the XOR swizzle of tc_rswz and written by consecutive threads on
+// consecutive positions, each position's bucket from a stored byte (or from
+// the key again, for radix digits).
+template <int KIND, bool PAIRS, int STAGES, int KPT, bool BULK>
 __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
     k_postscan_tc(const __grid_constant__ CUtensorMap tmk, const __grid_constant__ CUtensorMap tmv, TcPostArgs a) {
   static_assert(KPT == 8 || KPT == 16, "8 or 16 keys per thread");
-  using Lay = TcPostLayout<KIND, PAIRS, STAGES, KPT>;
+  using Lay = TcPostLayout<KIND, PAIRS, STAGES, KPT, BULK>;
   constexpr uint32_t T = Lay::T;
   extern __shared__ __align__(16) uint32_t smem_raw[];
   __shared__ __align__(8) uint64_t s_bar[STAGES];
   __shared__ uint32_t s_pend[STAGES];  // 1 + index of the tile whose copy is in flight in the slot, 0 if none
-  __shared__ uint32_t s_run[kTcMaxM], s_delta[kTcMaxM], s_start[kTcMaxM];
+  __shared__ uint32_t s_run[kTcMaxM], s_off[kTcMaxM], s_start[kTcMaxM], s_delta[kTcMaxM];
+  __shared__ __align__(16) uint32_t s_scr[2 * 8 * 32];  // scratch of chunk_offsets
   __shared__ __align__(16) uint32_t s_warp[8];
   const DevSpec& sp = a.sp;
   const uint32_t m = sp.m, R = tc_rows(m);
   const uint32_t sa = smem_addr(smem_raw);
   uint32_t* base = smem_raw + (((1024u - (sa & 1023u)) & 1023u) >> 2);
-  uint32_t* ring_k = base;
-  uint32_t* ring_v = base + STAGES * T;
-  uint32_t* s_cnt = base + Lay::cnt();
-  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(base + Lay::bkt(R));
-  uint32_t* s_tbl = base + Lay::tbl(R);
-  uint32_t* s_lut = base + Lay::lut(R);
+  uint32_t* ring = base;
+  constexpr uint32_t PART = Lay::kPart, SLOT = Lay::kSlotWords;
+  uint32_t* s_cnt = base + Lay::cnt(m);
+  uint8_t* s_bkt = reinterpret_cast<uint8_t*>(base + Lay::bkt(m));
+  uint32_t* s_tbl = base + Lay::tbl(m);
+  uint32_t* s_lut = base + Lay::lut(m);
 
   const uint32_t t = threadIdx.x;
   const TcLut L{s_lut, 32u - a.lb, a.lw, t & ((1u << a.lw) - 1u), (1u << (32u - a.lb)) - 1u, s_tbl};
@@ -456,15 +499,15 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
   // they are the ones still in L2
   auto tile_of = [&](uint32_t j) { return t1 - 1u - j; };
   auto is_full = [&](uint32_t j) { return (size_t)(tile_of(j) + 1u) * T <= a.n; };
-  const uint64_t pol = policy_evict_first();
 
   auto issue = [&](uint32_t j) {  // thread 0: start the copies of tile j into its slot
     if (!a.tma || j >= ntiles || !is_full(j)) return;
     const uint32_t slot = j % STAGES;
     const int y = (int)(tile_of(j) * (T / 32u));
+    const uint64_t pol = policy_evict_first();
     mbar_arrive_expect_tx(s_bar + slot, T * 4u * (PAIRS ? 2u : 1u));
-    tma_tile_2d(ring_k + slot * T, &tmk, 0, y, s_bar + slot, pol);
-    if constexpr (PAIRS) tma_tile_2d(ring_v + slot * T, &tmv, 0, y, s_bar + slot, pol);
+    tma_tile_2d(ring + slot * SLOT, &tmk, 0, y, s_bar + slot, pol);
+    if constexpr (PAIRS) tma_tile_2d(ring + slot * SLOT + PART, &tmv, 0, y, s_bar + slot, pol);
     s_pend[slot] = j + 1u;
   };
 
@@ -480,24 +523,23 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
   if (t == 0)
     for (uint32_t j = 0; j < (uint32_t)STAGES; ++j) issue(j);  // inputs are not written by the pre-scan
   tc_build_tables<KIND>(sp, a.lb, a.lw, s_tbl, s_lut);  // ends with a barrier
-  pdl_wait();  // H scanned by the pre-scan grid
-  const uint32_t len = m * a.G;
-  for (uint32_t b = t; b < m; b += kTcThreads) {
-    const uint32_t e = b * a.G + c;
-    s_run[b] = (e + 1u < len) ? a.Gx[e + 1u] : a.n;  // end of bucket b's share of this chunk
-  }
-  __syncthreads();
+  pdl_wait();  // H complete (the pre-scan grid has finished)
+  chunk_offsets(a.H, a.G, m, R, c, s_run, s_scr, a.offsets);
 
   uint32_t* my = s_cnt + t + ((t >> 5) << 2);  // counter (bucket 0, thread t)
   uint32_t phase = 0;                          // bit k: parity of slot k's next completion
+  // output addresses in words modulo 4: the runs are placed to match the keys'
+  // (the values take the bulk copies too when theirs is the same)
+  const uint32_t rk = (uint32_t)(reinterpret_cast<uintptr_t>(a.keys_out) >> 2) & 3u;
+  const bool vbulk = !PAIRS || (((uint32_t)(reinterpret_cast<uintptr_t>(a.vals_out) >> 2) & 3u) == rk);
 
   auto tile_body = [&](auto full_tag, uint32_t j) -> bool {
     constexpr bool FULL = decltype(full_tag)::value;
     const uint32_t tile = tile_of(j), slot = j % STAGES;
     const size_t tb = (size_t)tile * T;
     const uint32_t tile_n = FULL ? T : (uint32_t)((size_t)a.n - tb);
-    uint32_t* sk = ring_k + slot * T;
-    uint32_t* sv = ring_v + slot * T;
+    uint32_t* sk = ring + slot * SLOT;
+    uint32_t* sv = sk + PART;
     (void)sv;
     bool ok = true;
     if (FULL && a.tma) {
@@ -530,16 +572,22 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
       }
     }
     // (B) buckets
-    uint32_t flag = 0;
+    uint32_t any = 0;
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+    for (int i = 0; i < KPT; ++i) {
+      bk[i] = tc_bucket_marked<KIND>(key[i], sp, L);
+      any |= bk[i];
+    }
     if constexpr (KIND == kRange)
-      if (flag & kTcLutFlag) tc_fixup<KPT>(key, bk, L, s_tbl, m);
+      if (any >= 32u) tc_fix_marked<KPT>(key, bk, s_tbl, m);
     // (C) rank of each key among the earlier keys of its bucket in this thread
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
       if (FULL || KPT * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);
     }
+    // the previous tile's bulk copies out of the other slot have read it
+    if constexpr (BULK)
+      if (t < m) bulk_wait_read_all();
     if (__syncthreads_or(!ok)) return false;  // (1) counts complete; the previous tile is written out
     if (t == 0 && j > 0) {
       // the previous tile's slot is free again: refill it
@@ -581,13 +629,16 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
     }
     __syncthreads();  // (3) scanned counters and bucket starts visible
 
-    // (E) per bucket: global position minus tile position
+    // (E) per bucket: the run's global start, its offset in the reordered slot
+    uint32_t gs = 0, cnt = 0;
     if (t < m) {
       const uint32_t start = s_start[t];
       const uint32_t end = (t + 1u < m) ? s_start[t + 1u] : tile_n;
-      const uint32_t g = s_run[t] - (end - start);
-      s_run[t] = g;
-      s_delta[t] = g - start;
+      cnt = end - start;
+      gs = s_run[t] - cnt;
+      s_run[t] = gs;
+      s_delta[t] = gs - start;
+      if constexpr (BULK) s_off[t] = 4u * t + ((gs - start + rk) & 3u);
     }
     // positions, then clear this thread's counters (rows < m; the scan wrote
     // every one of them) for the next tile
@@ -596,42 +647,81 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
       if (FULL || KPT * t + i < tile_n) pos[i] += my[bk[i] * kTcRow];
     }
     for (uint32_t b = 0; b < m; ++b) my[b * kTcRow] = 0u;
+    if constexpr (BULK) __syncthreads();  // (3b) s_off visible
     // (F) permute the tile in place (every thread read its keys before (1))
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
       if (FULL || KPT * t + i < tile_n) {
         const uint32_t p = pos[i];
         if (p < T) {
-          sk[tc_rswz(p)] = key[i];
-          if constexpr (PAIRS) sv[tc_rswz(p)] = val[i];
-          if constexpr (!cheap_bucket<KIND>()) s_bkt[tc_rswz(p)] = (uint8_t)bk[i];
+          if constexpr (BULK) {
+            const uint32_t q = p + s_off[bk[i]];
+            sk[q] = key[i];
+            if constexpr (PAIRS) sv[q] = val[i];
+          } else {
+            const uint32_t q = tc_rswz(p);
+            sk[q] = key[i];
+            if constexpr (PAIRS) sv[q] = val[i];
+            if constexpr (Lay::kBytes) s_bkt[q] = (uint8_t)bk[i];
+          }
         } else {
           atomicOr(a.err, kDevErrBounds);
         }
       }
     }
-    __syncthreads();  // (4)
+    if constexpr (BULK) fence_proxy_async_smem();  // the permuted tile, for the bulk copies
+    __syncthreads();                               // (4)
 
-    // (G) consecutive threads write consecutive positions of each bucket run
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const uint32_t p = t + k * kTcThreads;
-      if (FULL || p < tile_n) {
-        const uint32_t q = tc_rswz(p);
-        const uint32_t kq = sk[q];
-        uint32_t b;
-        if constexpr (cheap_bucket<KIND>()) {
-          uint32_t unused = 0;
-          b = tc_bucket<KIND>(kq, sp, L, unused);
-        } else {
-          b = s_bkt[q];
-        }
-        const uint32_t g = s_delta[b] + p;
-        if (g < a.n) {
-          __stcs(a.keys_out + g, kq);
-          if constexpr (PAIRS) __stcs(a.vals_out + g, sv[q]);
+    if constexpr (BULK) {
+      // (G) thread b writes bucket b's run: the 16-byte-aligned interior by
+      // one bulk copy, the ends by plain stores
+      if (t < m && cnt > 0u) {
+        if ((size_t)gs + cnt <= a.n) {
+          const uint32_t q0 = s_start[t] + s_off[t];  // the run in the slot
+          const uint32_t ge = gs + cnt;
+          // [a0, a1): the positions whose output addresses are 16-byte aligned
+          const uint32_t a0 = min(ge, gs + ((4u - ((gs + rk) & 3u)) & 3u));
+          const uint32_t a1 = max(a0, ge - ((ge + rk) & 3u));
+          if (a1 > a0) {
+            const uint64_t pol = policy_evict_first();
+            bulk_s2g(a.keys_out + a0, sk + q0 + (a0 - gs), (a1 - a0) * 4u, pol);
+            if (PAIRS && vbulk) bulk_s2g(a.vals_out + a0, sv + q0 + (a0 - gs), (a1 - a0) * 4u, pol);
+          }
+          bulk_commit();
+          auto put = [&](uint32_t g) {
+            __stcs(a.keys_out + g, sk[q0 + (g - gs)]);
+            if constexpr (PAIRS) __stcs(a.vals_out + g, sv[q0 + (g - gs)]);
+          };
+          for (uint32_t g = gs; g < a0; ++g) put(g);
+          for (uint32_t g = a1; g < ge; ++g) put(g);
+          if constexpr (PAIRS)  // values aligned unlike the keys: plain stores for the interior too
+            if (!vbulk)
+              for (uint32_t g = a0; g < a1; ++g) __stcs(a.vals_out + g, sv[q0 + (g - gs)]);
         } else {
           atomicOr(a.err, kDevErrBounds);
+        }
+      }
+    } else {
+      // (G) consecutive threads write consecutive positions of each bucket run
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        const uint32_t p = t + k * kTcThreads;
+        if (FULL || p < tile_n) {
+          const uint32_t q = tc_rswz(p);
+          const uint32_t kq = sk[q];
+          uint32_t b;
+          if constexpr (Lay::kBytes) {
+            b = s_bkt[q];
+          } else {
+            b = tc_bucket_marked<KIND>(kq, sp, L);
+          }
+          const uint32_t g = s_delta[b] + p;
+          if (g < a.n) {
+            __stcs(a.keys_out + g, kq);
+            if constexpr (PAIRS) __stcs(a.vals_out + g, sv[q]);
+          } else {
+            atomicOr(a.err, kDevErrBounds);
+          }
         }
       }
     }
@@ -645,10 +735,14 @@ __global__ void __launch_bounds__(kTcThreads, KPT == 8 ? 3 : 2)
       if (t == 0)
         for (int k = 0; k < STAGES; ++k)
           if (s_pend[k] != 0u) mbar_drain(s_bar + k, (phase >> k) & 1u);
+      if constexpr (BULK)
+        if (t < m) bulk_wait_all();
       __syncthreads();
       return;
     }
   }
+  if constexpr (BULK)
+    if (t < m) bulk_wait_all();  // shared memory must outlive the bulk copies reading it
 }
 
 }  // namespace ms
