@@ -309,6 +309,19 @@ ms_status ms_tune_reset(void);
 ms_status ms_tune_set_sort(int pairs, int size_class, int method);
 ms_status ms_tune_get_sort(int pairs, int size_class, int *method);
 
+/* The kernel of batched plans (not in the paper), per (bucket kind, pairs 0/1,
+ * ceil(log2 m) in 0..8, size class of the plan's mean segment length as for
+ * ms_tune_size_class): rank 2 = per-thread bucket counters (m <= 32, shape
+ * 0 only), 1 = per-warp peer tables, 3 = peers found by ballots with per-warp
+ * counters; shape 0 = 8 warps x 16 keys per lane, 1 = 16 warps x 8 keys
+ * (both 4096-key tiles).  Read when a plan is created (ms_batch_plan_create,
+ * ms_batch_plan_create_dynamic, and the plans of ms_multisplit_pairs_batched);
+ * unset entries use rank 2 for m <= 32 and rank 1 beyond, shape 0.
+ * MS_ERR_INVALID_ARG for out-of-range arguments.  ms_tune_reset clears these
+ * entries too. */
+ms_status ms_tune_set_batch(int kind, int pairs, int log2m, int size_class, int shape, int rank);
+ms_status ms_tune_get_batch(int kind, int pairs, int log2m, int size_class, int *shape, int *rank);
+
 /* Human-readable name of a status code (static storage). */
 const char *ms_status_string(ms_status s);
 

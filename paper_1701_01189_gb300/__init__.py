@@ -11,6 +11,7 @@ from ._binding import (  # noqa: F401
     ms_device_status, ms_histogram, histogram, ms_multisplit_keys, ms_multisplit_keys_noalloc, ms_multisplit_pairs, ms_radix_sort, ms_radix_sort_r, ms_stage_times, ms_stage_timing,
     ms_status_string, ms_test_expire_lookback, ms_test_expire_lookback_noalloc, ms_noalloc_status, ms_shutdown,
     ms_multisplit_pairs_batched, segment_records, ms_tune_get, ms_tune_get_sort, ms_tune_reset, ms_tune_set, ms_tune_set_sort, ms_tune_size_class,
+    ms_tune_set_batch, ms_tune_get_batch,
     ms_version,
     multisplit_keys, multisplit_pairs, radix_sort,
 )

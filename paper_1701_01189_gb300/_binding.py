@@ -91,7 +91,10 @@ def lib() -> ctypes.CDLL:
         L.ms_tune_reset.argtypes = []
         L.ms_tune_set_sort.argtypes = [I, I, I]
         L.ms_tune_get_sort.argtypes = [I, I, P]
-        for f in ("ms_tune_set", "ms_tune_get", "ms_tune_reset", "ms_tune_set_sort", "ms_tune_get_sort"):
+        L.ms_tune_set_batch.argtypes = [I, I, I, I, I, I]
+        L.ms_tune_get_batch.argtypes = [I, I, I, I, P, P]
+        for f in ("ms_tune_set", "ms_tune_get", "ms_tune_reset", "ms_tune_set_sort", "ms_tune_get_sort",
+                  "ms_tune_set_batch", "ms_tune_get_batch"):
             getattr(L, f).restype = ctypes.c_int
         L.ms_batch_plan_create.argtypes = [ctypes.POINTER(_Segment), ctypes.c_uint32, SP, ctypes.POINTER(P)]
         L.ms_batch_plan_create_dynamic.argtypes = [ctypes.c_uint32, ctypes.c_uint64, I, SP, ctypes.POINTER(P)]
@@ -227,6 +230,17 @@ def ms_tune_get_sort(pairs: int, size_class: int) -> int:
     v = ctypes.c_int()
     _check(lib().ms_tune_get_sort(pairs, size_class, ctypes.byref(v)), "ms_tune_get_sort")
     return v.value
+
+
+def ms_tune_set_batch(kind: int, pairs: int, log2m: int, size_class: int, shape: int, rank: int) -> int:
+    return lib().ms_tune_set_batch(kind, pairs, log2m, size_class, shape, rank)
+
+
+def ms_tune_get_batch(kind: int, pairs: int, log2m: int, size_class: int):
+    """(status, shape, rank) of the batched variant table entry."""
+    sh, rk = ctypes.c_int(), ctypes.c_int()
+    st = lib().ms_tune_get_batch(kind, pairs, log2m, size_class, ctypes.byref(sh), ctypes.byref(rk))
+    return st, sh.value, rk.value
 
 
 def ms_status_string(status: int) -> str:

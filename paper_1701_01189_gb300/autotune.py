@@ -123,14 +123,88 @@ def tune_sort(n: int, pairs: bool, reps: int = 3):
     return (int(pairs), sc), best, times
 
 
-def save(entries, path: str = DEFAULT_PATH, sort_entries=()):
+def batch_variants(log2m: int):
+    """(shape, rank) candidates of the batched kernel: per-thread counters
+    (m <= 32), peer tables and ballot peers in both tile shapes."""
+    out = [(0, 2)] if log2m <= 5 else []
+    for shape in (0, 1):
+        out += [(shape, 1), (shape, 3)]
+    return out
+
+
+def tune_batch(kind_name: str, m: int, pairs: bool, segments: int = 1024, seg_log2=(8.0, 20.0), reps: int = 5):
+    """Times every batched-kernel variant on a plan of `segments` segments of
+    floor(2^U) keys, U ~ U(seg_log2) (the batched configuration's size law),
+    through the CUDA-graph replay; installs the fastest for the key (kind,
+    pairs, ceil(log2 m), size class of the mean segment) with
+    ms_tune_set_batch and returns (key, best, {variant: ms})."""
+    import numpy as np
+    import torch
+
+    import synthetic
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sizes = synthetic.segment_sizes(segments, seg_log2[0], seg_log2[1], 2024)
+    total = int(sizes.sum())
+    gen = synthetic.uniform_f32_1000 if kind_name == "delta" else synthetic.uniform_u32
+    kall = torch.from_numpy(gen(total, 2025).view(np.int32)).to(dev)
+    vall = torch.zeros_like(kall) if pairs else None
+    ko = torch.empty_like(kall)
+    vo = torch.empty_like(kall) if pairs else None
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    segs = []
+    for s0, n_ in zip(starts, sizes):
+        o = 4 * int(s0)
+        segs.append((kall.data_ptr() + o, vall.data_ptr() + o if pairs else None, ko.data_ptr() + o,
+                     vo.data_ptr() + o if pairs else None, None, int(n_)))
+    spec = _spec(kind_name, m, dev)
+    cs = spec.c()
+    log2m = (m - 1).bit_length()
+    kind = spec.kind if m > 1 else B.RADIX
+    sc = B.ms_tune_size_class(total // segments)
+    stream = torch.cuda.current_stream().cuda_stream
+    times = {}
+    for v in batch_variants(log2m):
+        B._check(B.ms_tune_set_batch(kind, int(pairs), log2m, sc, *v), "ms_tune_set_batch")
+        st, plan = B.ms_batch_plan_create(segs, cs)
+        B._check(st, "ms_batch_plan_create")
+        try:
+            times[v] = _time_call(lambda: B._check(B.ms_batch_run_graph(plan, stream), "ms_batch_run_graph"), reps)
+        finally:
+            B.ms_batch_plan_destroy(plan)
+    best = min(times, key=times.get)
+    B._check(B.ms_tune_set_batch(kind, int(pairs), log2m, sc, *best), "ms_tune_set_batch")
+    return (kind, int(pairs), log2m, sc), best, times
+
+
+def _spec(kind_name: str, m: int, dev):
+    import numpy as np
+    import torch
+
+    import synthetic
+
+    if kind_name == "radix":
+        bits = (m - 1).bit_length()
+        return B.BucketSpec.radix(32 - bits, bits)
+    if kind_name == "range":
+        spl = synthetic.range_splitters(m, 3)
+        return B.BucketSpec.range_u32(torch.from_numpy(spl.view(np.int32)).to(dev))
+    if kind_name == "mod":
+        return B.BucketSpec.mod(m)
+    return B.BucketSpec.delta_f32(m, float(np.float32(1000.0) / np.float32(m)))
+
+
+def save(entries, path: str = DEFAULT_PATH, sort_entries=(), batch_entries=()):
     """entries: list of (key, variant) pairs as returned by tune_workload;
-    sort_entries: list of (key, method) pairs as returned by tune_sort."""
+    sort_entries: list of (key, method) pairs as returned by tune_sort;
+    batch_entries: list of (key, (shape, rank)) pairs as returned by tune_batch."""
     data = [{"kind": k[0], "pairs": k[1], "log2m": k[2], "size_class": k[3], "shape": v[0], "rank": v[1],
              "reorder": v[2]} for k, v in entries]
     sort = [{"pairs": k[0], "size_class": k[1], "method": m} for k, m in sort_entries]
+    batch = [{"kind": k[0], "pairs": k[1], "log2m": k[2], "size_class": k[3], "shape": v[0], "rank": v[1]}
+             for k, v in batch_entries]
     with open(path, "w") as f:
-        json.dump({"format": 1, "entries": data, "sort": sort}, f, indent=1)
+        json.dump({"format": 1, "entries": data, "sort": sort, "batch": batch}, f, indent=1)
 
 
 def load(path: str = DEFAULT_PATH) -> int:
@@ -145,6 +219,8 @@ def load(path: str = DEFAULT_PATH) -> int:
         count += st == B.MS_OK
     for e in data.get("sort", []):
         count += B.ms_tune_set_sort(e["pairs"], e["size_class"], e["method"]) == B.MS_OK
+    for e in data.get("batch", []):
+        count += B.ms_tune_set_batch(e["kind"], e["pairs"], e["log2m"], e["size_class"], e["shape"], e["rank"]) == B.MS_OK
     return count
 
 
@@ -194,10 +270,28 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser(description="measure the multisplit kernel variants and save the fastest per workload")
     ap.add_argument("--out", default=DEFAULT_PATH)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--only-batch", action="store_true",
+                    help="tune the batched kernels only, keeping the other entries of the table at --out")
     args = ap.parse_args()
     from .build import build
 
     build()
+    batch_entries = []
+    for kind_name in ("mod", "range"):
+        for m in (2, 8, 32, 64, 256):
+            for pairs in (False, True):
+                key, best, times = tune_batch(kind_name, m, pairs, reps=args.reps)
+                batch_entries.append((key, best))
+                print(f"batched {kind_name} m={m} {'pairs' if pairs else 'keys'}: best {best} "
+                      f"({', '.join(f'{k}: {v:.3f} ms' for k, v in times.items())})", flush=True)
+    if args.only_batch:
+        old = json.load(open(args.out)) if os.path.exists(args.out) else {}
+        entries = [((e["kind"], e["pairs"], e["log2m"], e["size_class"]), (e["shape"], e["rank"], e["reorder"]))
+                   for e in old.get("entries", [])]
+        sort_entries = [((e["pairs"], e["size_class"]), e["method"]) for e in old.get("sort", [])]
+        save(entries, args.out, sort_entries, batch_entries)
+        print("saved", args.out)
+        raise SystemExit(0)
     entries = tune_suite(reps=args.reps)
     sort_entries = []
     for n_log2 in (22, 28):
@@ -206,5 +300,5 @@ if __name__ == "__main__":
             sort_entries.append((key, best))
             print(f"sort n=2^{n_log2} {'pairs' if pairs else 'keys'}: best method {best} "
                   f"({', '.join(f'{k}: {v:.3f} ms' for k, v in times.items())})", flush=True)
-    save(entries, args.out, sort_entries)
+    save(entries, args.out, sort_entries, batch_entries)
     print("saved", args.out)

@@ -69,23 +69,27 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 // Shared memory (words): splitter table 256, LUT, s_base 256, s_delta 256,
 // s_warp 32, counters NW*257, peer tables 2*NW*256, tile keys T, tile values T
 // (pairs), reorder keys T, values T (pairs), bucket bytes T.
-template <int KIND, bool PAIRS>
+template <int KIND, bool PAIRS, int NW>
 struct BatchLayout {
   static constexpr uint32_t T = kBatchTile;
   static __host__ __device__ uint32_t lut() { return 256; }
   static __host__ __device__ uint32_t base(uint32_t lb) { return lut() + lut_words<KIND>(lb); }
   static __host__ __device__ uint32_t cnt(uint32_t lb) { return base(lb) + 256 + 256 + 32; }
-  static __host__ __device__ uint32_t peer(uint32_t lb) { return cnt(lb) + kBatchNW * 257; }
-  static __host__ __device__ uint32_t tile(uint32_t lb) { return (peer(lb) + 2 * kBatchNW * 256 + 3) & ~3u; }
+  static __host__ __device__ uint32_t peer(uint32_t lb) { return cnt(lb) + NW * 257; }
+  static __host__ __device__ uint32_t tile(uint32_t lb) { return (peer(lb) + 2 * NW * 256 + 3) & ~3u; }
   static __host__ __device__ uint32_t reorder(uint32_t lb) { return tile(lb) + T * (PAIRS ? 2 : 1); }
   static __host__ size_t bytes(uint32_t lb) { return 4u * (size_t)(reorder(lb) + T * (PAIRS ? 2 : 1)) + T; }
 };
 
-template <int KIND, bool PAIRS>
-__global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArgs a) {
-  using Lay = BatchLayout<KIND, PAIRS>;
+// NW warps of ITEMS windows each (NW * 32 * ITEMS = 4096 keys a tile); ranks
+// by per-warp peer tables (RANK = kRankTable) or by ballot peers with
+// per-warp counters (kRankVote).
+template <int KIND, bool PAIRS, int NW, int ITEMS, int RANK>
+__global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(BatchArgs a) {
+  static_assert(NW * 32 * ITEMS == (int)kBatchTile, "a tile is 4096 keys");
+  using Lay = BatchLayout<KIND, PAIRS, NW>;
   constexpr uint32_t T = Lay::T;
-  constexpr int THREADS = kBatchNW * 32;
+  constexpr int THREADS = NW * 32;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_item, s_flag;
   const DevSpec& sp = a.sp;
@@ -105,10 +109,10 @@ __global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArg
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t* wc = s_cnt + w * S;
   uint32_t* wpeer = s_peer + w * 2 * m_pad;
-  const uint32_t off0 = w * (32 * kBatchItems) + lane;
+  const uint32_t off0 = w * (32 * ITEMS) + lane;
   const uint32_t lane_x[1] = {0u};
 
-  for (uint32_t i = threadIdx.x; i < 2 * kBatchNW * m_pad; i += THREADS) s_peer[i] = 0u;
+  for (uint32_t i = threadIdx.x; i < 2 * NW * m_pad; i += THREADS) s_peer[i] = 0u;
   build_bucket_tables<KIND, 8>(sp, s_tbl, s_lut);  // ends with a barrier
   const uint2 counts = a.items[0];  // read from memory so a captured graph follows later updates
   const uint32_t n_hist = counts.x, n_items = counts.y;
@@ -131,16 +135,16 @@ __global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArg
         if (it >= n_hist) t_vals[p] = __ldcs(sg.vin + tbase + p);
     }
     __syncthreads();
-    const uint32_t avail = tile_n - min(tile_n, w * (32u * kBatchItems));
-    uint32_t rb[kBatchItems];
+    const uint32_t avail = tile_n - min(tile_n, w * (32u * ITEMS));
+    uint32_t rb[ITEMS];
     if (tile_n == T)
-      rank_windows<KIND, 8, kBatchItems, kRankTable, true>(t_keys + off0, avail, sp, s_tbl, s_lut, wc, wpeer, m_pad,
+      rank_windows<KIND, 8, ITEMS, RANK, true>(t_keys + off0, avail, sp, s_tbl, s_lut, wc, wpeer, m_pad,
                                                           m, lane_x, lanemask_lt(), lane, rb);
     else
-      rank_windows<KIND, 8, kBatchItems, kRankTable, false>(t_keys + off0, avail, sp, s_tbl, s_lut, wc, wpeer,
+      rank_windows<KIND, 8, ITEMS, RANK, false>(t_keys + off0, avail, sp, s_tbl, s_lut, wc, wpeer,
                                                            m_pad, m, lane_x, lanemask_lt(), lane, rb);
     __syncthreads();
-    const uint32_t total = scan_tile_counters<kBatchNW>(s_cnt, S, m_pad, s_warp);
+    const uint32_t total = scan_tile_counters<NW>(s_cnt, S, m_pad, s_warp);
 
     if (it < n_hist) {
       // (A) tile histogram -> column `tile` of the segment's H
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArg
           const uint32_t e = base + threadIdx.x;
           const uint32_t v = e < len ? __ldcg(Hs + e) : 0u;
           uint32_t tot;
-          const uint32_t ex = block_exclusive_scan<kBatchNW>(v, s_warp, &tot);
+          const uint32_t ex = block_exclusive_scan<NW>(v, s_warp, &tot);
           if (e < len) {
             Hs[e] = carry + ex;
             if (sg.offsets != nullptr && e % sg.L == 0u) sg.offsets[e / sg.L] = carry + ex;
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArg
     if (threadIdx.x < m) s_delta[threadIdx.x] = s_base[threadIdx.x] - s_cnt[threadIdx.x];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kBatchItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       if (off0 + i * 32 < tile_n) {
         const uint32_t b = rb[i] >> 16;
         const uint32_t p = wc[b] + (rb[i] & 0xffffu);
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kBatchNW * 32, PAIRS ? 2 : 3) k_batch(BatchArg
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kBatchItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const uint32_t p = threadIdx.x + k * THREADS;
       if (p < tile_n) {
         const uint32_t g = s_delta[s_bkt[p]] + p;
@@ -254,6 +258,7 @@ struct ms_batch_plan {
   uint32_t grid = 0;
   size_t smem = 0;
   uint32_t lb = 0, lw = 0;  // m <= 32: splitter lookup table of k_batch_tc
+  int shape = 0, rank = 0;  // the kernel (from the batched variant table, see choose_batch_variant)
   DevSeg* d_segs = nullptr;
   uint2* d_items = nullptr;  // [0] = (n_hist, n_items), then the items
   uint32_t* d_H = nullptr;
@@ -269,30 +274,33 @@ struct ms_batch_plan {
 
 namespace ms {
 
-template <int KIND, bool PAIRS>
-static cudaError_t batch_setup(ms_batch_plan& p, int sm_count) {
-  if (p.sp.m <= kTcMaxM) {
-    auto k = k_batch_tc<KIND, PAIRS>;
-    p.lb = 9;
-    p.lw = (PAIRS && p.sp.m > 16) ? 1u : 2u;
-    p.smem = BatchTcLayout<KIND, PAIRS>::bytes(p.sp.m, p.lb, p.lw);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-    if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kTcThreads, p.smem);
-    if (e != cudaSuccess) return e;
-    p.grid = (uint32_t)std::max(1, nb) * (uint32_t)sm_count;
-    return cudaSuccess;
-  }
-  auto k = k_batch<KIND, PAIRS>;
-  p.smem = BatchLayout<KIND, PAIRS>::bytes(p.sp.lut_bits);
+template <typename K>
+static cudaError_t batch_occupancy(ms_batch_plan& p, K k, int threads, int sm_count) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBatchNW * 32, p.smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, p.smem);
   if (e != cudaSuccess) return e;
   p.grid = (uint32_t)std::max(1, nb) * (uint32_t)sm_count;
   return cudaSuccess;
+}
+
+template <int KIND, bool PAIRS>
+static cudaError_t batch_setup(ms_batch_plan& p, int sm_count) {
+  if (p.rank == kRankThread) {
+    p.lb = 9;
+    p.lw = (PAIRS && p.sp.m > 16) ? 1u : 2u;
+    p.smem = BatchTcLayout<KIND, PAIRS>::bytes(p.sp.m, p.lb, p.lw);
+    return batch_occupancy(p, k_batch_tc<KIND, PAIRS>, kTcThreads, sm_count);
+  }
+  if (p.shape == 1) {
+    p.smem = BatchLayout<KIND, PAIRS, 16>::bytes(p.sp.lut_bits);
+    if (p.rank == kRankVote) return batch_occupancy(p, k_batch<KIND, PAIRS, 16, 8, kRankVote>, 512, sm_count);
+    return batch_occupancy(p, k_batch<KIND, PAIRS, 16, 8, kRankTable>, 512, sm_count);
+  }
+  p.smem = BatchLayout<KIND, PAIRS, 8>::bytes(p.sp.lut_bits);
+  if (p.rank == kRankVote) return batch_occupancy(p, k_batch<KIND, PAIRS, 8, 16, kRankVote>, 256, sm_count);
+  return batch_occupancy(p, k_batch<KIND, PAIRS, 8, 16, kRankTable>, 256, sm_count);
 }
 
 template <int KIND, bool PAIRS>
@@ -306,10 +314,16 @@ static cudaError_t batch_launch(const ms_batch_plan& p, cudaStream_t s) {
   a.ticket = p.d_flags + 2 * p.max_segments;
   a.err = p.d_err;
   a.sp = p.sp;
-  if (p.sp.m <= kTcMaxM)
+  if (p.rank == kRankThread)
     k_batch_tc<KIND, PAIRS><<<p.grid, kTcThreads, p.smem, s>>>(a, p.lb, p.lw);
+  else if (p.shape == 1 && p.rank == kRankVote)
+    k_batch<KIND, PAIRS, 16, 8, kRankVote><<<p.grid, 512, p.smem, s>>>(a);
+  else if (p.shape == 1)
+    k_batch<KIND, PAIRS, 16, 8, kRankTable><<<p.grid, 512, p.smem, s>>>(a);
+  else if (p.rank == kRankVote)
+    k_batch<KIND, PAIRS, 8, 16, kRankVote><<<p.grid, 256, p.smem, s>>>(a);
   else
-    k_batch<KIND, PAIRS><<<p.grid, kBatchNW * 32, p.smem, s>>>(a);
+    k_batch<KIND, PAIRS, 8, 16, kRankTable><<<p.grid, 256, p.smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -399,7 +413,7 @@ static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec&
 
 // Allocates a plan's device memory for the given capacities.
 static ms_status plan_alloc(ms_batch_plan* p, DeviceCtx* ctx, int kind, bool pairs, const DevSpec& sp,
-                            uint32_t max_segments, uint32_t max_items, uint64_t max_hwords) {
+                            uint32_t max_segments, uint32_t max_items, uint64_t max_hwords, uint64_t mean_n) {
   p->device = ctx->device;
   if (p->device >= 0 && p->device < 64) g_live_plans[p->device].fetch_add(1);
   p->kind = kind;
@@ -408,6 +422,9 @@ static ms_status plan_alloc(ms_batch_plan* p, DeviceCtx* ctx, int kind, bool pai
   p->d_err = ctx->d_err;
   p->max_segments = max_segments;
   p->max_items = max_items;
+  const Variant v = choose_batch_variant(kind, pairs, sp.nbits, mean_n);
+  p->rank = (v.rank == kRankThread && sp.m > kTcMaxM) ? kRankTable : v.rank;
+  p->shape = p->rank == kRankThread ? 0 : v.shape;
   p->max_hwords = max_hwords;
   p->flags_bytes = ((size_t)2 * max_segments + 4) * 4;
   cudaError_t e = cudaMalloc(&p->d_segs, std::max<size_t>(1, max_segments) * sizeof(DevSeg));
@@ -444,8 +461,11 @@ extern "C" ms_status ms_batch_plan_create(const ms_segment* segs, uint32_t num_s
   DeviceCtx* ctx = nullptr;
   st = current_device_ctx(&ctx);
   if (st != MS_OK) return st;
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < num_segments; ++i) total += segs[i].n;
   auto* p = new ms_batch_plan();
-  st = plan_alloc(p, ctx, kind, pairs, sp, num_segments, (uint32_t)(items.size() - 1), hwords);
+  st = plan_alloc(p, ctx, kind, pairs, sp, num_segments, (uint32_t)(items.size() - 1), hwords,
+                  num_segments ? total / num_segments : 0);
   p->num_segments = num_segments;
   p->n_items = items[0].y;
   cudaError_t e = cudaSuccess;
@@ -478,7 +498,8 @@ extern "C" ms_status ms_batch_plan_create_dynamic(uint32_t max_segments, uint64_
   st = current_device_ctx(&ctx);
   if (st != MS_OK) return st;
   auto* p = new ms_batch_plan();
-  st = plan_alloc(p, ctx, kind, pairs != 0, sp, max_segments, (uint32_t)(2 * tiles), (uint64_t)sp.m * tiles);
+  st = plan_alloc(p, ctx, kind, pairs != 0, sp, max_segments, (uint32_t)(2 * tiles), (uint64_t)sp.m * tiles,
+                  max_elements / max_segments);
   const size_t stage_bytes = (size_t)max_segments * sizeof(DevSeg) + ((size_t)2 * tiles + 1) * sizeof(uint2);
   for (int k = 0; k < 2 && st == MS_OK; ++k) {
     if (cudaMallocHost(&p->h_stage[k], stage_bytes) != cudaSuccess ||

@@ -8,7 +8,8 @@
 // then one post-scan item per tile.  Differences: a histogram item only
 // counts (one shared atomic per key, no ranks), and every CTA copies the next
 // item's tile into the other of two shared-memory slots with asynchronous
-// 4-byte copies (any alignment) while it works on the current one.  Items
+// asynchronous copies while it works on the current one (16-byte copies
+// for the chunks of any segment phase, see copy_tile_shifted).  Items
 // are taken by ticket, three tickets ahead of the current item; a waiting
 // post-scan item only waits for histogram items, whose tickets are all
 // smaller and whose holders never wait, so every wait ends.
@@ -21,18 +22,71 @@ namespace ms {
 __device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Dynamic shared memory (words): two slots (keys T, then values T for pairs),
-// counters R * 288, bucket bytes (T), splitter table 32, lookup table.
+// Copies the n <= T words at src (4-byte aligned, any phase) into a slot
+// region: word p lands at tc_swz(p + r), r = the word phase of src modulo 4,
+// so that src's 16-byte chunks land on 16-byte chunks of the region and go
+// by 16-byte copies; the at most 3 words before the first chunk and after the
+// last go by 4-byte copies.  The region needs T + 32 words.  All threads of
+// the block call it.
+__device__ __forceinline__ void copy_tile_shifted(uint32_t* dst, const uint32_t* src, uint32_t n) {
+  const uint32_t t = threadIdx.x;
+  const uint32_t r = (uint32_t)(reinterpret_cast<uintptr_t>(src) >> 2) & 3u;
+  const uint32_t h = min(n, (4u - r) & 3u);  // head words
+  const uint32_t nch = (n - h) >> 2;         // whole 16-byte chunks after the head
+  for (uint32_t k = t; k < nch; k += kTcThreads) {
+    const uint32_t p = h + 4u * k;
+    cp_async16(dst + tc_swz(p + r), src + p);
+  }
+  const uint32_t tail0 = h + 4u * nch;
+  if (t < h) cp_async4(dst + tc_swz(t + r), src + t);
+  if (t >= 4u && t - 4u < n - tail0) cp_async4(dst + tc_swz(tail0 + (t - 4u) + r), src + tail0 + (t - 4u));
+}
+
+// The 16 words of positions [16t, 16t+16) of a region filled by
+// copy_tile_shifted with phase r (uniform over the block): five 16-byte
+// loads and a shift by r.
+__device__ __forceinline__ void read16_shifted(const uint32_t* region, uint32_t r, uint32_t (&out)[16]) {
+  uint32_t w[20];
+  const uint32_t t = threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const uint4 v = *reinterpret_cast<const uint4*>(region + tc_swz(16u * t + 4u * c));
+    w[4 * c + 0] = v.x;
+    w[4 * c + 1] = v.y;
+    w[4 * c + 2] = v.z;
+    w[4 * c + 3] = v.w;
+  }
+  switch (r) {
+#define MS_SHIFT_CASE(R)                                 \
+  case R:                                                \
+    _Pragma("unroll") for (int e = 0; e < 16; ++e) out[e] = w[e + R]; \
+    break;
+    MS_SHIFT_CASE(0)
+    MS_SHIFT_CASE(1)
+    MS_SHIFT_CASE(2)
+    default:
+      _Pragma("unroll") for (int e = 0; e < 16; ++e) out[e] = w[e + 3];
+#undef MS_SHIFT_CASE
+  }
+}
+
+// Dynamic shared memory (words): two slots (keys T + 32, then values T + 32
+// for pairs), counters R * 288, bucket bytes (T), splitter table 32, lookup
+// table.
 template <int KIND, bool PAIRS>
 struct BatchTcLayout {
   static constexpr uint32_t T = kTcTile;
-  static constexpr uint32_t kSlotWords = T * (PAIRS ? 2 : 1);
+  static constexpr uint32_t kRegion = T + 32;
+  static constexpr uint32_t kSlotWords = kRegion * (PAIRS ? 2 : 1);
   static __host__ __device__ uint32_t cnt() { return 2 * kSlotWords; }
   static __host__ __device__ uint32_t bkt(uint32_t R) { return cnt() + R * kTcRow; }
   static __host__ __device__ uint32_t tbl(uint32_t R) { return bkt(R) + T / 4; }
@@ -76,11 +130,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
       const size_t tb = (size_t)item.y * T;
       const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
       uint32_t* sk = smem + slot * SW;
-      const bool vals = PAIRS && it >= n_hist;
-      for (uint32_t p = t; p < tile_n; p += kTcThreads) {
-        cp_async4(sk + tc_swz(p), sg.kin + tb + p);
-        if (vals) cp_async4(sk + T + tc_swz(p), sg.vin + tb + p);
-      }
+      copy_tile_shifted(sk, sg.kin + tb, tile_n);
+      if (PAIRS && it >= n_hist) copy_tile_shifted(sk + Lay::kRegion, sg.vin + tb, tile_n);
     }
     cp_async_commit();
   };
@@ -123,18 +174,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
     const size_t tb = (size_t)tile * T;
     const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
     uint32_t* sk = smem + slot * SW;
-    uint32_t* sv = sk + T;
+    uint32_t* sv = sk + Lay::kRegion;
     (void)sv;
 
     uint32_t key[16], bk[16];
-#pragma unroll
-    for (int j4 = 0; j4 < 4; ++j4) {
-      const uint4 v = *reinterpret_cast<const uint4*>(sk + tc_swz(16u * t + 4u * j4));
-      key[4 * j4 + 0] = v.x;
-      key[4 * j4 + 1] = v.y;
-      key[4 * j4 + 2] = v.z;
-      key[4 * j4 + 3] = v.w;
-    }
+    read16_shifted(sk, (uint32_t)(reinterpret_cast<uintptr_t>(sg.kin + tb) >> 2) & 3u, key);
     uint32_t flag = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
@@ -201,16 +245,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
     } else {
       // (B) post-scan of one tile
       uint32_t val[PAIRS ? 16 : 1], pos[16];
-      if constexpr (PAIRS) {
-#pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4) {
-          const uint4 x = *reinterpret_cast<const uint4*>(sv + tc_swz(16u * t + 4u * j4));
-          val[4 * j4 + 0] = x.x;
-          val[4 * j4 + 1] = x.y;
-          val[4 * j4 + 2] = x.z;
-          val[4 * j4 + 3] = x.w;
-        }
-      }
+      if constexpr (PAIRS) read16_shifted(sv, (uint32_t)(reinterpret_cast<uintptr_t>(sg.vin + tb) >> 2) & 3u, val);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         if (16u * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);

@@ -47,6 +47,11 @@ struct Variant {
 int size_class(uint32_t n);
 // The tuned (or default) variant for a request (ms_tune.cu).
 Variant choose_variant(const Call& c);
+// The tuned (or default) kernel of a batched plan for its identifier and mean
+// segment length: rank kRankThread (k_batch_tc, m <= 32), kRankTable or
+// kRankVote (k_batch) and, for k_batch, the tile shape (0: 8 warps x 16 keys,
+// 1: 16 warps x 8 keys) (ms_tune.cu).
+Variant choose_batch_variant(int kind, bool pairs, uint32_t nbits, uint64_t mean_n);
 // How the radix sort makes its passes: 0 one-sweep kernels, 1 three-stage
 // multisplits with the radix-digit identifier (ms_tune.cu).
 int choose_sort_method(uint32_t n, bool pairs);

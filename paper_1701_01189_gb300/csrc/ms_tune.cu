@@ -3,6 +3,7 @@
 // ceil(log2 m), size class of n).  Defaults come from the rules below; the
 // autotuner (paper_1701_01189_gb300/autotune.py) measures the candidates on the
 // device and installs the fastest with ms_tune_set().
+#include <algorithm>
 #include <mutex>
 
 #include "ms.h"
@@ -18,6 +19,17 @@ Variant g_table[kKinds][2][kNbits][kClasses];
 // radix sort passes per (pairs, size class): 0 one-sweep, 1 three-stage multisplits
 bool g_sort_set[2][kClasses] = {};
 int g_sort[2][kClasses];
+// batched plans per (kind, pairs, ceil(log2 m), size class of the mean segment)
+bool g_batch_set[kKinds][2][kNbits][kClasses] = {};
+Variant g_batch[kKinds][2][kNbits][kClasses];
+
+Variant default_batch_variant(int nbits) {
+  Variant v;
+  v.shape = 0;
+  v.rank = nbits <= 5 ? kRankThread : kRankTable;
+  v.reorder = 1;
+  return v;
+}
 
 // Up to 32 buckets: per-thread bucket counters (ms_tc.cuh).  Beyond, peer
 // tables with block reordering; key-value pairs prefer the smaller 8 x 8 tile
@@ -57,9 +69,42 @@ Variant choose_variant(const Call& c) {
   return default_variant(nb, pairs);
 }
 
+Variant choose_batch_variant(int kind, bool pairs, uint32_t nbits, uint64_t mean_n) {
+  const int sc = size_class((uint32_t)std::min<uint64_t>(mean_n, 0xffffffffu)), p = pairs ? 1 : 0;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (kind >= 0 && kind < kKinds && nbits < (uint32_t)kNbits && g_batch_set[kind][p][nbits][sc])
+    return g_batch[kind][p][nbits][sc];
+  return default_batch_variant((int)nbits);
+}
+
 }  // namespace ms
 
 using namespace ms;
+
+extern "C" ms_status ms_tune_set_batch(int kind, int pairs, int nbits, int sclass, int shape, int rank) {
+  if (kind < 0 || kind >= kKinds || pairs < 0 || pairs > 1 || nbits < 0 || nbits >= kNbits || sclass < 0 ||
+      sclass >= kClasses || shape < 0 || shape > 1 || !(rank == kRankTable || rank == kRankThread || rank == kRankVote))
+    return MS_ERR_INVALID_ARG;
+  if (rank == kRankThread && (nbits > 5 || shape != 0)) return MS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_batch[kind][pairs][nbits][sclass] = Variant{shape, rank, 1};
+  g_batch_set[kind][pairs][nbits][sclass] = true;
+  return MS_OK;
+}
+
+extern "C" ms_status ms_tune_get_batch(int kind, int pairs, int nbits, int sclass, int* shape, int* rank) {
+  if (kind < 0 || kind >= kKinds || pairs < 0 || pairs > 1 || nbits < 0 || nbits >= kNbits || sclass < 0 ||
+      sclass >= kClasses)
+    return MS_ERR_INVALID_ARG;
+  Variant v;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    v = g_batch_set[kind][pairs][nbits][sclass] ? g_batch[kind][pairs][nbits][sclass] : default_batch_variant(nbits);
+  }
+  if (shape) *shape = v.shape;
+  if (rank) *rank = v.rank;
+  return MS_OK;
+}
 
 extern "C" int ms_tune_size_class(size_t n) { return n >= ((size_t)1 << 32) ? 3 : size_class((uint32_t)n); }
 
@@ -98,6 +143,10 @@ extern "C" ms_status ms_tune_reset(void) {
         for (auto& d : c) d = false;
   for (auto& a : g_sort_set)
     for (auto& b : a) b = false;
+  for (auto& a : g_batch_set)
+    for (auto& b : a)
+      for (auto& c : b)
+        for (auto& d : c) d = false;
   return MS_OK;
 }
 

@@ -132,6 +132,53 @@ def test_batch_config_4096_segments_full_size():
     assert torch.equal(pk, ko) and torch.equal(pvo, vo) and torch.equal(poffs, offs)
 
 
+BATCH_VARIANT_CASES = [Case(oracle.MOD, 32), Case(oracle.RANGE_U32, 256, splitters=synthetic.range_splitters(256, 5)),
+                       Case(oracle.DELTA_F32, 8, x0=0.0, delta=float(np.float32(1000.0) / np.float32(8)))]
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+@pytest.mark.parametrize("ci", range(3), ids=["mod32", "range256", "delta8"])
+def test_every_batched_kernel_variant(ci, pairs):
+    """Each kernel the batched variant table can select (per-thread counters,
+    peer tables or ballot peers; 8 x 16 or 16 x 8 tiles), forced for this
+    identifier, against the oracle; the table is restored afterwards."""
+    import torch
+
+    import paper_1701_01189_gb300 as ms
+    from paper_1701_01189_gb300 import autotune
+
+    case = BATCH_VARIANT_CASES[ci]
+    sizes = SIZES + [200_000, 65_536]
+    keys = [synthetic.uniform_f32_1000(n, 40 + i) if case.kind == oracle.DELTA_F32 else synthetic.uniform_u32(n, 40 + i)
+            for i, n in enumerate(sizes)]
+    vals = [synthetic.index_values(n) for n in sizes] if pairs else None
+    dk = [to_dev(k) for k in keys]
+    dv = [to_dev(v) for v in vals] if pairs else None
+    log2m = (case.m - 1).bit_length()
+    expect = [oracle.multisplit(keys[i], None if vals is None else vals[i], case.oracle_spec()) for i in range(len(sizes))]
+    try:
+        for shape, rank in autotune.batch_variants(log2m):
+            for sc in range(4):
+                assert ms.ms_tune_set_batch(case.kind, int(pairs), log2m, sc, shape, rank) == ms.MS_OK
+            plan = ms.BatchPlan(dk, dv, case.gpu_spec())
+            try:
+                plan.run(graph=True)
+                torch.cuda.synchronize()
+                assert ms.device_status() == ms.MS_OK
+                for i, n in enumerate(sizes):
+                    ok, ov, ooff = expect[i]
+                    what = f"variant ({shape}, {rank}) segment {i} n={n}"
+                    np.testing.assert_array_equal(to_host(plan.keys_out[i]), ok, err_msg=what)
+                    if pairs:
+                        np.testing.assert_array_equal(to_host(plan.vals_out[i]), ov, err_msg=what)
+                    np.testing.assert_array_equal(to_host(plan.offsets[i]).astype(np.uint64), ooff, err_msg=what)
+            finally:
+                plan.close()
+    finally:
+        ms.ms_tune_reset()
+        autotune.load()
+
+
 def test_batch_rejects_mixed_segments():
     import paper_1701_01189_gb300 as ms
 

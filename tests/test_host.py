@@ -172,6 +172,17 @@ def test_tuning_table_validation_and_defaults(lib):
     assert ms.ms_tune_set_sort(1, 3, 2) == ms.MS_ERR_INVALID_ARG and ms.ms_tune_set_sort(2, 3, 1) == ms.MS_ERR_INVALID_ARG
     ms.ms_tune_reset()
     assert ms.ms_tune_get_sort(1, 3) == 0
+    # batched kernels: counters for m <= 32, peer tables beyond, by default
+    assert ms.ms_tune_get_batch(ms.MOD, 1, 5, 2) == (ms.MS_OK, 0, 2)
+    assert ms.ms_tune_get_batch(ms.MOD, 1, 8, 2) == (ms.MS_OK, 0, 1)
+    assert ms.ms_tune_set_batch(ms.MOD, 1, 8, 2, 0, 2) == ms.MS_ERR_INVALID_ARG  # counters need log2 m <= 5
+    assert ms.ms_tune_set_batch(ms.MOD, 1, 5, 2, 1, 2) == ms.MS_ERR_INVALID_ARG  # counters: 8 x 16 only
+    assert ms.ms_tune_set_batch(ms.MOD, 1, 5, 2, 2, 1) == ms.MS_ERR_INVALID_ARG  # shapes 0, 1
+    assert ms.ms_tune_set_batch(ms.MOD, 1, 5, 2, 0, 0) == ms.MS_ERR_INVALID_ARG  # no plain ballots
+    assert ms.ms_tune_set_batch(ms.MOD, 1, 5, 2, 1, 3) == ms.MS_OK
+    assert ms.ms_tune_get_batch(ms.MOD, 1, 5, 2) == (ms.MS_OK, 1, 3)
+    ms.ms_tune_reset()
+    assert ms.ms_tune_get_batch(ms.MOD, 1, 5, 2) == (ms.MS_OK, 0, 2)
 
 
 def test_shipped_tuning_table_is_valid(lib):
@@ -184,7 +195,7 @@ def test_shipped_tuning_table_is_valid(lib):
     try:
         if os.path.exists(autotune.DEFAULT_PATH):
             d = json.load(open(autotune.DEFAULT_PATH))
-            n = len(d["entries"]) + len(d.get("sort", []))
+            n = len(d["entries"]) + len(d.get("sort", [])) + len(d.get("batch", []))
             assert autotune.load() == n > 0
     finally:
         ms.ms_tune_reset()
