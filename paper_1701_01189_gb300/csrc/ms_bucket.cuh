@@ -212,14 +212,16 @@ __device__ __forceinline__ uint32_t wide_bucket(uint32_t u, const DevSpec& sp, c
   return (b >> sp.dshift) & sp.dmask;
 }
 
-// Identifiers whose bucket costs two ALU instructions (the radix digit): the
-// post-scans recompute it from the reordered key at write-out instead of
-// storing a bucket byte per position (a scattered shared-memory store and a
-// load).  Measured on GB300: 4-9% faster sorts; for delta buckets the
-// recomputation was up to 9% slower, so the others keep the byte.
-template <int KIND>
+// Identifiers whose bucket the post-scans recompute from the reordered key at
+// write-out instead of storing a bucket byte per position (a scattered
+// shared-memory store and a load).  The radix digit costs two ALU
+// instructions: 4-9% faster sorts on GB300.  The modulo bucket costs a
+// multiply-high, a multiply and a subtract: recomputing it is 4% faster for
+// key-value pairs with 32 or 64 buckets and no faster for keys alone.  For
+// delta buckets the recomputation was up to 9% slower, so they keep the byte.
+template <int KIND, bool PAIRS>
 __host__ __device__ constexpr bool cheap_bucket() {
-  return KIND == kRadix;
+  return KIND == kRadix || (PAIRS && KIND == kMod);
 }
 
 // Builds the splitter table (2^NB - 1 words) and, for range buckets, the

@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
           if (p < T) {
             s_keys[p] = rk[off0 + i * 32];
             if constexpr (PAIRS) s_vals[p] = rv[off0 + i * 32];
-            if constexpr (!cheap_bucket<KIND>()) s_bkt[p] = (uint8_t)b;
+            if constexpr (!cheap_bucket<KIND, PAIRS>()) s_bkt[p] = (uint8_t)b;
           } else {
             atomicOr(a.err, kDevErrBounds);
           }
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_postscan(PostscanArgs a) {
         if (FULL || p < tile_n) {
           const uint32_t kq = s_keys[p];
           uint32_t b;
-          if constexpr (cheap_bucket<KIND>())
+          if constexpr (cheap_bucket<KIND, PAIRS>())
             b = bucket_of<KIND, NB>(kq, sp, s_tbl, s_lut);
           else
             b = s_bkt[p];

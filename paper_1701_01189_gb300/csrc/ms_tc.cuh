@@ -216,8 +216,19 @@ __host__ size_t tc_prescan_smem(uint32_t m, uint32_t lb, uint32_t lw) {
   return 4u * (size_t)(cnt_words + tbl_words + tc_lut_words(KIND, lb, lw));
 }
 
+// Tiles of keys in flight per thread in the pre-scan's main loop.  Range
+// buckets (a lookup-table probe and a splitter compare per key) gain from a
+// third tile at two CTAs per SM (3-4 us of 68 at 2^26 keys on GB300); delta
+// buckets lost 15 us that way and modulo buckets nothing, so they keep two
+// tiles at three CTAs per SM.
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k_prescan_tc(TcPreArgs a) {
+__host__ __device__ constexpr int tc_prescan_depth() {
+  return (KIND == kRange && MODE != kCountLaneBytes) ? 3 : 2;
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kTcThreads, (MODE == kCountLaneBytes || tc_prescan_depth<KIND, MODE>() == 3) ? 2 : 3)
+    k_prescan_tc(TcPreArgs a) {
   constexpr int BB = MODE == kCountLaneBytes ? 8 : 5;  // bits of a bucket in the lookup table
   constexpr int NW = kTcThreads / 32;
   extern __shared__ __align__(16) uint32_t smem[];
@@ -312,17 +323,21 @@ __global__ void __launch_bounds__(kTcThreads, MODE == kCountLaneBytes ? 2 : 3) k
   // counts tiles [t0, t1) of chunk c and adds them into its column of H
   auto piece = [&](uint32_t c, uint32_t t0, uint32_t t1) {
     const uint32_t tv1 = a.vec ? max(t0, min(t1, nfull)) : t0;
-    // full, aligned tiles: 16-byte loads, the next tile's loads in flight
-    // while this one is counted
+    // full, aligned tiles: 16-byte loads, the next D - 1 tiles' loads in
+    // flight while this one is counted
     if (t0 < tv1) {
-      uint32_t ka[16], kb[16];
-      load16(ka, t0);
-      for (uint32_t tile = t0; tile < tv1; tile += 2) {
-        if (tile + 1 < tv1) load16(kb, tile + 1);
-        count16(ka);
-        if (tile + 1 >= tv1) break;
-        if (tile + 2 < tv1) load16(ka, tile + 2);
-        count16(kb);
+      constexpr int D = tc_prescan_depth<KIND, MODE>();
+      uint32_t kbuf[D][16];
+#pragma unroll
+      for (int d = 0; d < D - 1; ++d)
+        if (t0 + d < tv1) load16(kbuf[d], t0 + d);
+      for (uint32_t tile = t0; tile < tv1; tile += D) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          if (tile + d >= tv1) break;
+          if (tile + d + D - 1 < tv1) load16(kbuf[(d + D - 1) % D], tile + d + D - 1);
+          count16(kbuf[d]);
+        }
       }
     }
     // the partial last tile, or every tile of an unaligned input (at most 16
@@ -418,7 +433,7 @@ struct TcPostLayout {
   static constexpr uint32_t kSlotWords = kPart * (PAIRS ? 2u : 1u);
   // a bucket byte per reordered position for the write-out without bulk
   // copies, unless the identifier is cheap to evaluate again
-  static constexpr bool kBytes = !BULK && !cheap_bucket<KIND>();
+  static constexpr bool kBytes = !BULK && !cheap_bucket<KIND, PAIRS>();
   static __host__ __device__ uint32_t cnt(uint32_t) { return STAGES * kSlotWords; }
   static __host__ __device__ uint32_t bkt(uint32_t m) { return cnt(m) + tc_rows(m) * kTcRow; }
   static __host__ __device__ uint32_t tbl(uint32_t m) { return bkt(m) + (kBytes ? T / 4 : 0u); }
