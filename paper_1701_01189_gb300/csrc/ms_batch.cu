@@ -5,16 +5,18 @@
 // the three stages once per array is dominated by launch latency (cf. the
 // small-frontier overhead the paper notes for SSSP, Section 7.2).
 //
-// A plan flattens every segment into a list of tile work items, in two
-// groups: (A) the histogram of each tile of every segment that spans more than
-// one tile, and (B) the post-scan of every tile of every segment, where a
-// segment of a single tile is done in one item from start to finish (its own
-// tile histogram is the whole H, so no global scan is needed).  CTAs of one
-// persistent grid take items in ticket order.  The CTA that finishes the last
-// histogram of a segment scans that segment's histogram matrix (bucket-major,
-// one column per tile: Eq. 2 with the segment's tiles as subproblems) and
-// raises the segment's ready flag; post-scan items of the segment wait for
-// that flag (bounded).  Every item a CTA waits for has an earlier ticket, so
+// A plan flattens every segment into a list of work items, each a run of up
+// to K consecutive 4096-key tiles of one segment (a chunk; K = 1 for the
+// peer-table kernel, kBatchChunkTiles for the per-thread-counter kernel), in
+// two groups: (A) the histogram of each chunk of every segment that spans
+// more than one tile, and (B) the post-scan of every chunk of every segment,
+// where a segment of a single tile is done in one item from start to finish
+// (its own tile histogram is the whole H, so no global scan is needed).  CTAs
+// of one persistent grid take items in ticket order.  The CTA that finishes
+// the last histogram of a segment scans that segment's histogram matrix
+// (bucket-major, one column per chunk: Eq. 2 with the segment's chunks as
+// subproblems) and raises the segment's ready flag; post-scan items of the
+// segment wait for that flag (bounded).  Every item a CTA waits for has an earlier ticket, so
 // it belongs to a CTA that is already running: the waits always end.
 #include <algorithm>
 #include <atomic>
@@ -33,6 +35,10 @@ namespace ms {
 
 constexpr int kBatchNW = 8, kBatchItems = 16;
 constexpr uint32_t kBatchTile = kBatchNW * 32 * kBatchItems;  // 4096
+// tiles per work item of the per-thread-counter kernel: a post-scan item
+// pays its ready-flag wait and descriptor loads, and a histogram item its
+// fence, done-counter atomic and H write, once per chunk instead of per tile
+constexpr uint32_t kBatchChunkTiles = 8;
 
 struct DevSeg {
   const uint32_t* kin;
@@ -43,17 +49,18 @@ struct DevSeg {
   uint32_t n;
   uint32_t L;         // tiles
   uint32_t hoff;      // first word of the segment's H in the plan's pool (multi-tile only)
-  uint32_t pad;
+  uint32_t C;         // chunks of K tiles: the columns of the segment's H (m x C words)
 };
 
 struct BatchArgs {
   const DevSeg* segs;
-  const uint2* items;    // items[0] = (n_hist, n_items); then (segment, tile) pairs, histograms first
+  const uint2* items;    // items[0] = (n_hist, n_items); then (segment, first tile) pairs, histograms first
   uint32_t* H;           // histogram pool
   uint32_t* done;        // per segment: histogram items finished (zeroed per run)
   uint32_t* ready;       // per segment: scan finished (zeroed per run)
   uint32_t* ticket;      // zeroed per run
   uint32_t* err;
+  uint32_t K;            // tiles per item (the last item of a segment may hold fewer)
   DevSpec sp;
 };
 
@@ -151,17 +158,17 @@ __global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(Bat
       if (threadIdx.x < m) {
         const uint32_t b = threadIdx.x;
         const uint32_t hist = ((b + 1 < m_pad) ? s_cnt[b + 1] : total) - s_cnt[b];
-        a.H[sg.hoff + b * sg.L + tile] = hist;
+        a.H[sg.hoff + b * sg.C + tile] = hist;
       }
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) s_flag = (atomicAdd(a.done + item.x, 1u) == sg.L - 1) ? 1u : 0u;
+      if (threadIdx.x == 0) s_flag = (atomicAdd(a.done + item.x, 1u) == sg.C - 1) ? 1u : 0u;
       __syncthreads();
       if (s_flag) {
         // last histogram of the segment: exclusive scan of its H (m*L words,
         // bucket-major), bucket offsets, then the ready flag
         __threadfence();
-        const uint32_t len = m * sg.L;
+        const uint32_t len = m * sg.C;
         uint32_t* Hs = a.H + sg.hoff;
         uint32_t carry = 0;
         for (uint32_t base = 0; base < len; base += THREADS) {
@@ -171,7 +178,7 @@ __global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(Bat
           const uint32_t ex = block_exclusive_scan<NW>(v, s_warp, &tot);
           if (e < len) {
             Hs[e] = carry + ex;
-            if (sg.offsets != nullptr && e % sg.L == 0u) sg.offsets[e / sg.L] = carry + ex;
+            if (sg.offsets != nullptr && e % sg.C == 0u) sg.offsets[e / sg.C] = carry + ex;
           }
           carry += tot;
         }
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(Bat
         }
       }
       __syncthreads();
-      if (threadIdx.x < m) s_base[threadIdx.x] = __ldcg(a.H + sg.hoff + threadIdx.x * sg.L + tile);
+      if (threadIdx.x < m) s_base[threadIdx.x] = __ldcg(a.H + sg.hoff + threadIdx.x * sg.C + tile);
     }
     if (threadIdx.x < m) s_delta[threadIdx.x] = s_base[threadIdx.x] - s_cnt[threadIdx.x];
     __syncthreads();
@@ -259,6 +266,7 @@ struct ms_batch_plan {
   size_t smem = 0;
   uint32_t lb = 0, lw = 0;  // m <= 32: splitter lookup table of k_batch_tc
   int shape = 0, rank = 0;  // the kernel (from the batched variant table, see choose_batch_variant)
+  uint32_t K = 1;           // tiles per work item
   DevSeg* d_segs = nullptr;
   uint2* d_items = nullptr;  // [0] = (n_hist, n_items), then the items
   uint32_t* d_H = nullptr;
@@ -313,6 +321,7 @@ static cudaError_t batch_launch(const ms_batch_plan& p, cudaStream_t s) {
   a.ready = p.d_flags + p.max_segments;
   a.ticket = p.d_flags + 2 * p.max_segments;
   a.err = p.d_err;
+  a.K = p.K;
   a.sp = p.sp;
   if (p.rank == kRankThread)
     k_batch_tc<KIND, PAIRS><<<p.grid, kTcThreads, p.smem, s>>>(a, p.lb, p.lw);
@@ -365,10 +374,20 @@ static void plan_free(ms_batch_plan* p) {
 
 namespace ms {
 
-// Validates segs and builds the segment table and the work list (histogram
-// items first).  Returns the histogram words needed in *hwords.
-static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec& sp, bool pairs, DevSeg* hs,
-                            std::vector<uint2>& items, uint64_t* hwords) {
+// The kernel a plan runs and its tiles per work item.
+static void plan_kernel(int kind, bool pairs, const DevSpec& sp, uint64_t mean_n, int* rank, int* shape,
+                        uint32_t* K) {
+  const Variant v = choose_batch_variant(kind, pairs, sp.nbits, mean_n);
+  *rank = (v.rank == kRankThread && sp.m > kTcMaxM) ? kRankTable : v.rank;
+  *shape = *rank == kRankThread ? 0 : v.shape;
+  *K = *rank == kRankThread ? kBatchChunkTiles : 1u;
+}
+
+// Validates segs and builds the segment table and the work list of items of
+// up to K tiles (histogram items first).  Returns the histogram words needed
+// in *hwords.
+static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec& sp, bool pairs, uint32_t K,
+                            DevSeg* hs, std::vector<uint2>& items, uint64_t* hwords) {
   std::vector<uint2> post;
   items.clear();
   items.push_back(make_uint2(0u, 0u));  // counts, filled below
@@ -395,12 +414,13 @@ static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec&
     d.n = (uint32_t)g.n;
     // an empty segment still gets one (empty) item: it writes zero offsets
     d.L = std::max<uint32_t>(1u, (uint32_t)((g.n + kBatchTile - 1) / kBatchTile));
+    d.C = (d.L + K - 1) / K;
     if (d.L > 1) {
       d.hoff = (uint32_t)hw;
-      hw += (uint64_t)sp.m * d.L;
-      for (uint32_t t = 0; t < d.L; ++t) items.push_back(make_uint2(i, t));
+      hw += (uint64_t)sp.m * d.C;
+      for (uint32_t t = 0; t < d.L; t += K) items.push_back(make_uint2(i, t));
     }
-    for (uint32_t t = 0; t < d.L; ++t) post.push_back(make_uint2(i, t));
+    for (uint32_t t = 0; t < d.L; t += K) post.push_back(make_uint2(i, t));
     hs[i] = d;
   }
   const uint32_t n_hist = (uint32_t)(items.size() - 1);
@@ -422,9 +442,7 @@ static ms_status plan_alloc(ms_batch_plan* p, DeviceCtx* ctx, int kind, bool pai
   p->d_err = ctx->d_err;
   p->max_segments = max_segments;
   p->max_items = max_items;
-  const Variant v = choose_batch_variant(kind, pairs, sp.nbits, mean_n);
-  p->rank = (v.rank == kRankThread && sp.m > kTcMaxM) ? kRankTable : v.rank;
-  p->shape = p->rank == kRankThread ? 0 : v.shape;
+  plan_kernel(kind, pairs, sp, mean_n, &p->rank, &p->shape, &p->K);
   p->max_hwords = max_hwords;
   p->flags_bytes = ((size_t)2 * max_segments + 4) * 4;
   cudaError_t e = cudaMalloc(&p->d_segs, std::max<size_t>(1, max_segments) * sizeof(DevSeg));
@@ -453,19 +471,22 @@ extern "C" ms_status ms_batch_plan_create(const ms_segment* segs, uint32_t num_s
   if (st != MS_OK) return st;
   bool pairs = false;  // key-value if any segment carries values
   for (uint32_t i = 0; i < num_segments; ++i) pairs = pairs || segs[i].vals_in != nullptr;
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < num_segments; ++i) total += segs[i].n;
+  const uint64_t mean_n = num_segments ? total / num_segments : 0;
+  int rank = 0, shape = 0;
+  uint32_t K = 1;
+  plan_kernel(kind, pairs, sp, mean_n, &rank, &shape, &K);
   std::vector<DevSeg> hs(num_segments);
   std::vector<uint2> items;
   uint64_t hwords = 0;
-  st = build_work(segs, num_segments, sp, pairs, hs.data(), items, &hwords);
+  st = build_work(segs, num_segments, sp, pairs, K, hs.data(), items, &hwords);
   if (st != MS_OK) return st;
   DeviceCtx* ctx = nullptr;
   st = current_device_ctx(&ctx);
   if (st != MS_OK) return st;
-  uint64_t total = 0;
-  for (uint32_t i = 0; i < num_segments; ++i) total += segs[i].n;
   auto* p = new ms_batch_plan();
-  st = plan_alloc(p, ctx, kind, pairs, sp, num_segments, (uint32_t)(items.size() - 1), hwords,
-                  num_segments ? total / num_segments : 0);
+  st = plan_alloc(p, ctx, kind, pairs, sp, num_segments, (uint32_t)(items.size() - 1), hwords, mean_n);
   p->num_segments = num_segments;
   p->n_items = items[0].y;
   cudaError_t e = cudaSuccess;
@@ -525,7 +546,7 @@ extern "C" ms_status ms_batch_plan_set_segments(ms_batch_plan* plan, const ms_se
   DevSeg* hs = static_cast<DevSeg*>(plan->h_stage[k]);
   std::vector<uint2> items;
   uint64_t hwords = 0;
-  ms_status st = build_work(segs, num_segments, plan->sp, plan->pairs, hs, items, &hwords);
+  ms_status st = build_work(segs, num_segments, plan->sp, plan->pairs, plan->K, hs, items, &hwords);
   if (st != MS_OK) return st;
   if (items.size() - 1 > plan->max_items || hwords > plan->max_hwords) return MS_ERR_INVALID_ARG;
   uint2* hi = reinterpret_cast<uint2*>(static_cast<char*>(plan->h_stage[k]) +

@@ -120,14 +120,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
   const uint2 counts = a.items[0];  // read from memory so a captured graph follows later updates
   const uint32_t n_hist = counts.x, n_items = counts.y;
 
-  // all threads: copy item `it`'s tile (keys; values for a key-value
-  // post-scan) into `slot`, laid out as ms_tc.cuh's swizzled tiles; one
-  // commit group per call, empty or not
-  auto fetch = [&](uint32_t it, uint32_t slot) {
+  // all threads: copy tile t0 + j of item `it` (keys; values for a
+  // key-value post-scan) into `slot`, laid out as ms_tc.cuh's swizzled
+  // tiles; one commit group per call, empty or not
+  auto fetch = [&](uint32_t it, uint32_t j, uint32_t slot) {
     if (it < n_items) {
       const uint2 item = a.items[1 + it];
       const DevSeg sg = a.segs[item.x];
-      const size_t tb = (size_t)item.y * T;
+      const size_t tb = (size_t)(item.y + j) * T;
       const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
       uint32_t* sk = smem + slot * SW;
       copy_tile_shifted(sk, sg.kin + tb, tile_n);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
   // Tickets are taken three items ahead, and the descriptors of the later
   // items are pulled into L1 in two steps (the item entry, then the segment
   // it names) while the current item is worked on, so that the copy of the
-  // next item's tile starts without waiting on their loads.  (Holding
+  // next item's first tile starts without waiting on their loads.  (Holding
   // unstarted tickets is safe: a CTA holds histogram tickets only while it
   // works on a histogram item, which never waits.)
   auto prefetch_l1 = [](const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); };
@@ -153,43 +153,156 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
   __syncthreads();
   uint32_t cur = s_tk[0], nxt = s_tk[1], nxt2 = s_tk[2];
   uint32_t slot = 0;
-  fetch(cur, 0);
+  fetch(cur, 0, 0);
 
   while (cur < n_items) {
-    __syncthreads();  // the other slot's last item is written out; everyone read s_tk[3]
-    if (t == 0) {
-      if (nxt2 < n_items) prefetch_l1(a.segs + a.items[1 + nxt2].x);  // its entry came in an item ago
-      const uint32_t nn = atomicAdd(a.ticket, 1u);
-      s_tk[3] = nn;
-      if (nn < n_items) prefetch_l1(a.items + 1 + nn);
-    }
-    fetch(nxt, slot ^ 1u);
-    cp_async_wait<1>();  // this thread's copies of the current item landed
-    __syncthreads();     // everyone's
-    const uint32_t nn = s_tk[3];
-
     const uint2 item = a.items[1 + cur];
-    const uint32_t seg = item.x, tile = item.y;
+    const uint32_t seg = item.x, t0 = item.y;
     const DevSeg sg = a.segs[seg];
-    const size_t tb = (size_t)tile * T;
-    const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
-    uint32_t* sk = smem + slot * SW;
-    uint32_t* sv = sk + Lay::kRegion;
-    (void)sv;
+    const uint32_t t1 = min(t0 + a.K, sg.L), chunk = t0 / a.K;
+    const bool hist = cur < n_hist;
+    uint32_t nn = 0;    // the ticket taken during this item
+    uint32_t grun = 0;  // post-scan, thread b < m: global position of bucket b's next key of this chunk
 
-    uint32_t key[16], bk[16];
-    read16_shifted(sk, (uint32_t)(reinterpret_cast<uintptr_t>(sg.kin + tb) >> 2) & 3u, key);
-    uint32_t flag = 0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
-    if constexpr (KIND == kRange)
-      if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
+    for (uint32_t tile = t0; tile < t1; ++tile) {
+      const bool last = tile + 1u == t1;
+      __syncthreads();  // the other slot's tile is written out; everyone read s_tk[3]
+      if (last) {
+        if (t == 0) {
+          if (nxt2 < n_items) prefetch_l1(a.segs + a.items[1 + nxt2].x);  // its entry came in an item ago
+          const uint32_t tk = atomicAdd(a.ticket, 1u);
+          s_tk[3] = tk;
+          if (tk < n_items) prefetch_l1(a.items + 1 + tk);
+        }
+        fetch(nxt, 0, slot ^ 1u);
+      } else {
+        fetch(cur, tile + 1u - t0, slot ^ 1u);
+      }
+      cp_async_wait<1>();  // this thread's copies of the current tile landed
+      __syncthreads();     // everyone's
+      if (last) nn = s_tk[3];
 
-    if (cur < n_hist) {
-      // (A) tile histogram -> column `tile` of the segment's H
+      const size_t tb = (size_t)tile * T;
+      const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
+      uint32_t* sk = smem + slot * SW;
+      uint32_t* sv = sk + Lay::kRegion;
+      (void)sv;
+
+      uint32_t key[16], bk[16];
+      read16_shifted(sk, (uint32_t)(reinterpret_cast<uintptr_t>(sg.kin + tb) >> 2) & 3u, key);
+      uint32_t flag = 0;
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (16u * t + i < tile_n) atomicAdd(my + bk[i] * kTcRow, 1u);
+      for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+      if constexpr (KIND == kRange)
+        if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
+
+      if (hist) {
+        // (A) this tile's keys into the chunk's per-thread counts
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (16u * t + i < tile_n) atomicAdd(my + bk[i] * kTcRow, 1u);
+      } else {
+        // (B) post-scan of one tile
+        uint32_t val[PAIRS ? 16 : 1], pos[16];
+        if constexpr (PAIRS)
+          read16_shifted(sv, (uint32_t)(reinterpret_cast<uintptr_t>(sg.vin + tb) >> 2) & 3u, val);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (16u * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);
+        __syncthreads();
+        {
+          uint4* segc = reinterpret_cast<uint4*>(s_cnt + tc_pad(t * R));
+          uint32_t sum = 0;
+          for (uint32_t g = 0; g < R / 4u; ++g) {
+            const uint4 v = segc[g];
+            sum += v.x + v.y + v.z + v.w;
+          }
+          uint32_t total;
+          uint32_t run = tc_block_scan(sum, s_warp, &total);
+          if (((t * R) & 255u) == 0u) {
+            const uint32_t b = (t * R) >> 8;
+            if (b < m) s_start[b] = run;
+          }
+          for (uint32_t g = 0; t * R < m * 256u && g < R / 4u; ++g) {
+            const uint4 v = segc[g];
+            uint4 o;
+            o.x = run;
+            run += v.x;
+            o.y = run;
+            run += v.y;
+            o.z = run;
+            run += v.z;
+            o.w = run;
+            run += v.w;
+            segc[g] = o;
+          }
+        }
+        __syncthreads();
+        // global base of each bucket for this tile
+        if (t < m) {
+          const uint32_t start = s_start[t];
+          if (sg.L == 1u) {
+            s_delta[t] = 0u;  // the tile is the segment
+            if (sg.offsets != nullptr) {
+              sg.offsets[t] = start;
+              if (t == 0) sg.offsets[m] = tile_n;
+            }
+          } else {
+            if (tile == t0) {
+              uint32_t spins = 0;
+              while (ld_acquire_u32(a.ready + seg) == 0u) {
+                // give up at the bound, or at once when another wait has already given up
+                if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
+                  atomicOr(a.err, kDevErrTimeout);
+                  break;
+                }
+                __nanosleep(spins < 64 ? 64 : 512);
+              }
+              grun = __ldcg(a.H + sg.hoff + t * sg.C + chunk);
+            }
+            const uint32_t end = (t + 1u < m) ? s_start[t + 1u] : tile_n;
+            s_delta[t] = grun - start;
+            grun += end - start;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (16u * t + i < tile_n) pos[i] += my[bk[i] * kTcRow];
+        for (uint32_t b = 0; b < m; ++b) my[b * kTcRow] = 0u;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (16u * t + i < tile_n) {
+            const uint32_t p = pos[i];
+            if (p < T) {
+              sk[tc_rswz(p)] = key[i];
+              if constexpr (PAIRS) sv[tc_rswz(p)] = val[i];
+              s_bkt[tc_rswz(p)] = (uint8_t)bk[i];
+            } else {
+              atomicOr(a.err, kDevErrBounds);
+            }
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const uint32_t p = t + k * kTcThreads;
+          if (p < tile_n) {
+            const uint32_t q = tc_rswz(p);
+            const uint32_t g = s_delta[s_bkt[q]] + p;
+            if (g < sg.n) {
+              __stcs(sg.kout + g, sk[q]);
+              if constexpr (PAIRS) __stcs(sg.vout + g, sv[q]);
+            } else {
+              atomicOr(a.err, kDevErrBounds);
+            }
+          }
+        }
+      }
+      slot ^= 1u;
+    }
+
+    if (hist) {
+      // the chunk's counts -> column `chunk` of the segment's H
       __syncthreads();
       for (uint32_t b = w; b < m; b += kTcThreads / 32) {
         uint32_t* row = s_cnt + b * kTcRow + lane;
@@ -201,17 +314,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
-        if (lane == 0) a.H[sg.hoff + b * sg.L + tile] = s;
+        if (lane == 0) a.H[sg.hoff + b * sg.C + chunk] = s;
       }
       __threadfence();
       __syncthreads();
-      if (t == 0) s_flag = (atomicAdd(a.done + seg, 1u) == sg.L - 1u) ? 1u : 0u;
+      if (t == 0) s_flag = (atomicAdd(a.done + seg, 1u) == sg.C - 1u) ? 1u : 0u;
       __syncthreads();
       if (s_flag) {
-        // last histogram of the segment: exclusive scan of its H (m * L
+        // last histogram of the segment: exclusive scan of its H (m * C
         // words, bucket-major), bucket offsets, then the ready flag
         __threadfence();
-        const uint32_t len = m * sg.L;
+        const uint32_t len = m * sg.C;
         uint32_t* Hs = a.H + sg.hoff;
         uint32_t carry = 0;
         for (uint32_t base = 0; base < len; base += kTcTile) {
@@ -230,7 +343,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
             const uint32_t idx = base + 16u * t + i;
             if (idx < len) {
               Hs[idx] = run;
-              if (sg.offsets != nullptr && idx % sg.L == 0u) sg.offsets[idx / sg.L] = run;
+              if (sg.offsets != nullptr && idx % sg.C == 0u) sg.offsets[idx / sg.C] = run;
             }
             run += v[i];
           }
@@ -242,101 +355,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
         __syncthreads();
         if (t == 0) st_release_u32(a.ready + seg, 1u);
       }
-    } else {
-      // (B) post-scan of one tile
-      uint32_t val[PAIRS ? 16 : 1], pos[16];
-      if constexpr (PAIRS) read16_shifted(sv, (uint32_t)(reinterpret_cast<uintptr_t>(sg.vin + tb) >> 2) & 3u, val);
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (16u * t + i < tile_n) pos[i] = atomicAdd(my + bk[i] * kTcRow, 1u);
-      __syncthreads();
-      {
-        uint4* segc = reinterpret_cast<uint4*>(s_cnt + tc_pad(t * R));
-        uint32_t sum = 0;
-        for (uint32_t g = 0; g < R / 4u; ++g) {
-          const uint4 v = segc[g];
-          sum += v.x + v.y + v.z + v.w;
-        }
-        uint32_t total;
-        uint32_t run = tc_block_scan(sum, s_warp, &total);
-        if (((t * R) & 255u) == 0u) {
-          const uint32_t b = (t * R) >> 8;
-          if (b < m) s_start[b] = run;
-        }
-        for (uint32_t g = 0; t * R < m * 256u && g < R / 4u; ++g) {
-          const uint4 v = segc[g];
-          uint4 o;
-          o.x = run;
-          run += v.x;
-          o.y = run;
-          run += v.y;
-          o.z = run;
-          run += v.z;
-          o.w = run;
-          run += v.w;
-          segc[g] = o;
-        }
-      }
-      __syncthreads();
-      // global base of each bucket for this tile
-      if (t < m) {
-        const uint32_t start = s_start[t];
-        if (sg.L == 1u) {
-          s_delta[t] = 0u;  // the tile is the segment
-          if (sg.offsets != nullptr) {
-            sg.offsets[t] = start;
-            if (t == 0) sg.offsets[m] = tile_n;
-          }
-        } else {
-          uint32_t spins = 0;
-          while (ld_acquire_u32(a.ready + seg) == 0u) {
-            // give up at the bound, or at once when another wait has already given up
-            if (++spins > kSpinLimit || (spins > 64 && (*(volatile uint32_t*)a.err & kDevErrTimeout))) {
-              atomicOr(a.err, kDevErrTimeout);
-              break;
-            }
-            __nanosleep(spins < 64 ? 64 : 512);
-          }
-          s_delta[t] = __ldcg(a.H + sg.hoff + t * sg.L + tile) - start;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (16u * t + i < tile_n) pos[i] += my[bk[i] * kTcRow];
-      for (uint32_t b = 0; b < m; ++b) my[b * kTcRow] = 0u;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (16u * t + i < tile_n) {
-          const uint32_t p = pos[i];
-          if (p < T) {
-            sk[tc_rswz(p)] = key[i];
-            if constexpr (PAIRS) sv[tc_rswz(p)] = val[i];
-            s_bkt[tc_rswz(p)] = (uint8_t)bk[i];
-          } else {
-            atomicOr(a.err, kDevErrBounds);
-          }
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const uint32_t p = t + k * kTcThreads;
-        if (p < tile_n) {
-          const uint32_t q = tc_rswz(p);
-          const uint32_t g = s_delta[s_bkt[q]] + p;
-          if (g < sg.n) {
-            __stcs(sg.kout + g, sk[q]);
-            if constexpr (PAIRS) __stcs(sg.vout + g, sv[q]);
-          } else {
-            atomicOr(a.err, kDevErrBounds);
-          }
-        }
-      }
     }
     cur = nxt;
     nxt = nxt2;
     nxt2 = nn;
-    slot ^= 1u;
   }
   cp_async_wait<0>();  // nothing may be in flight into shared memory at exit
 }
