@@ -333,9 +333,9 @@ def run_gpu(args, rank: int, world: int):
 def e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n, world):
     """The same sweep through the C ABI with host buffers: each case copies its keys (and
     values) from pinned host memory, runs, and copies its outputs and offsets back into
-    pinned host memory.  Cases alternate between two streams, each with its own device
-    and host buffers, so one case's copies overlap the other's kernels (the usual
-    double-buffered pipeline a caller would write)."""
+    pinned host memory.  Cases rotate over `--e2e-lanes` streams, each with its own device
+    and host buffers, so one case's copies overlap the others' kernels and copies (the
+    usual multi-buffered pipeline a caller would write)."""
     pin = {}
     for cid, arr in hk.items():
         if id(arr) not in pin:
@@ -343,7 +343,8 @@ def e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n,
     hkeys = {cid: pin[id(arr)] for cid, arr in hk.items()}
     hv = torch.from_numpy(hvals.view(np.int32)).pin_memory()
     lanes = []
-    for _ in range(2):
+    nl = max(1, args.e2e_lanes)
+    for _ in range(nl):
         lanes.append({"stream": torch.cuda.Stream(device=dev),
                       "ho_k": torch.empty(n, dtype=torch.int32).pin_memory(),
                       "ho_v": torch.empty(n, dtype=torch.int32).pin_memory(),
@@ -358,7 +359,7 @@ def e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n,
     def step():
         nonlocal h2d, d2h
         for ci, (name, cid, kind, m, pairs) in enumerate(case_list):
-            L = lanes[ci % 2]
+            L = lanes[ci % nl]
             with torch.cuda.stream(L["stream"]):
                 sptr = L["stream"].cuda_stream
                 L["dk"].copy_(hkeys[cid], non_blocking=True)
@@ -407,7 +408,8 @@ def e2e_gpu(args, ms, metrics, torch, dev, hk, hspl, hvals, case_list, specs, n,
     value = metrics.rate_g(n * len(case_list) * steps * world, ms_total * 1e-3)
     return {"value": round(value, 3), "unit": "G elements/s (keys or pairs)",
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
-            "pipeline": "two streams, double-buffered (copies of one case overlap the other's kernels)"}
+            "pipeline": f"{nl} streams, each with its own buffers (copies of one case overlap the others' kernels "
+                        "and copies)"}
 
 
 # ----------------------------------------------------------------------------- other configurations
@@ -747,6 +749,7 @@ def main():
     ap.add_argument("--ref-sample-log2", type=int, default=20)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-lanes", type=int, default=3, help="streams (each with its own buffers) of the e2e pipeline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the nvidia-smi clock samples of the timed region are written")

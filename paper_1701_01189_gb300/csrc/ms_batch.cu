@@ -7,17 +7,20 @@
 //
 // A plan flattens every segment into a list of work items, each a run of up
 // to K consecutive 4096-key tiles of one segment (a chunk; K = 1 for the
-// peer-table kernel, kBatchChunkTiles for the per-thread-counter kernel), in
-// two groups: (A) the histogram of each chunk of every segment that spans
-// more than one tile, and (B) the post-scan of every chunk of every segment,
-// where a segment of a single tile is done in one item from start to finish
-// (its own tile histogram is the whole H, so no global scan is needed).  CTAs
-// of one persistent grid take items in ticket order.  The CTA that finishes
-// the last histogram of a segment scans that segment's histogram matrix
-// (bucket-major, one column per chunk: Eq. 2 with the segment's chunks as
-// subproblems) and raises the segment's ready flag; post-scan items of the
-// segment wait for that flag (bounded).  Every item a CTA waits for has an earlier ticket, so
-// it belongs to a CTA that is already running: the waits always end.
+// peer-table kernel, kBatchChunkTiles for the per-thread-counter kernel), of
+// two kinds: (A) the histogram of each chunk of every segment that spans more
+// than one tile, and (B) the post-scan of every chunk of every segment, where
+// a segment of a single tile is done in one item from start to finish (its
+// own tile histogram is the whole H, so no global scan is needed).  The list
+// holds the histogram items first, then the post-scan items (build_work).
+// CTAs of one persistent grid take
+// items in ticket order.  The CTA that finishes the last histogram of a
+// segment scans that segment's histogram matrix (bucket-major, one column per
+// chunk: Eq. 2 with the segment's chunks as subproblems) and raises the
+// segment's ready flag; post-scan items of the segment wait for that flag
+// (bounded).  Every item a post-scan item waits for has an earlier ticket and
+// never waits itself, so the waits always end (the argument is at
+// build_work).
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -39,6 +42,9 @@ constexpr uint32_t kBatchTile = kBatchNW * 32 * kBatchItems;  // 4096
 // pays its ready-flag wait and descriptor loads, and a histogram item its
 // fence, done-counter atomic and H write, once per chunk instead of per tile
 constexpr uint32_t kBatchChunkTiles = 8;
+// bit of an item's second word that marks a post-scan item (the rest is the
+// item's first tile)
+constexpr uint32_t kBatchPost = 1u << 31;
 
 struct DevSeg {
   const uint32_t* kin;
@@ -54,7 +60,7 @@ struct DevSeg {
 
 struct BatchArgs {
   const DevSeg* segs;
-  const uint2* items;    // items[0] = (n_hist, n_items); then (segment, first tile) pairs, histograms first
+  const uint2* items;    // items[0] = (n_hist, n_items); then (segment, first tile | kBatchPost for a post-scan)
   uint32_t* H;           // histogram pool
   uint32_t* done;        // per segment: histogram items finished (zeroed per run)
   uint32_t* ready;       // per segment: scan finished (zeroed per run)
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(Bat
   for (uint32_t i = threadIdx.x; i < 2 * NW * m_pad; i += THREADS) s_peer[i] = 0u;
   build_bucket_tables<KIND, 8>(sp, s_tbl, s_lut);  // ends with a barrier
   const uint2 counts = a.items[0];  // read from memory so a captured graph follows later updates
-  const uint32_t n_hist = counts.x, n_items = counts.y;
+  const uint32_t n_items = counts.y;
 
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.ticket, 1u);
@@ -131,7 +137,8 @@ __global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(Bat
     if (it >= n_items) break;
     const uint2 item = a.items[1 + it];
     const DevSeg sg = a.segs[item.x];
-    const uint32_t tile = item.y;
+    const uint32_t tile = item.y & ~kBatchPost;
+    const bool post = (item.y & kBatchPost) != 0u;
     const size_t tbase = (size_t)tile * T;
     const uint32_t tile_n = (uint32_t)min((size_t)T, (size_t)sg.n - tbase);
 
@@ -139,7 +146,7 @@ __global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(Bat
     for (uint32_t p = threadIdx.x; p < tile_n; p += THREADS) {
       t_keys[p] = __ldcs(sg.kin + tbase + p);
       if constexpr (PAIRS)
-        if (it >= n_hist) t_vals[p] = __ldcs(sg.vin + tbase + p);
+        if (post) t_vals[p] = __ldcs(sg.vin + tbase + p);
     }
     __syncthreads();
     const uint32_t avail = tile_n - min(tile_n, w * (32u * ITEMS));
@@ -153,7 +160,7 @@ __global__ void __launch_bounds__(NW * 32, (PAIRS ? 2 : 3) * 8 / NW) k_batch(Bat
     __syncthreads();
     const uint32_t total = scan_tile_counters<NW>(s_cnt, S, m_pad, s_warp);
 
-    if (it < n_hist) {
+    if (!post) {
       // (A) tile histogram -> column `tile` of the segment's H
       if (threadIdx.x < m) {
         const uint32_t b = threadIdx.x;
@@ -384,8 +391,17 @@ static void plan_kernel(int kind, bool pairs, const DevSpec& sp, uint64_t mean_n
 }
 
 // Validates segs and builds the segment table and the work list of items of
-// up to K tiles (histogram items first).  Returns the histogram words needed
-// in *hwords.
+// up to K tiles: the histogram items, then the post-scan items (measured on
+// GB300: interleaving waves of segments' histograms and post-scans, for the
+// post-scans to find their keys in L2, was slower -- post-scans waiting on
+// histograms still in progress -- and post-scans in reverse segment order no
+// faster).  Every post-scan item comes after all histogram items of its
+// segment, which is all the protocol needs:
+// if every running CTA were blocked, the one whose current item has the
+// smallest ticket would wait for a histogram item of a smaller ticket, held
+// by a CTA that is either working on it (histogram items never wait) or
+// blocked on an item of a still smaller ticket -- a contradiction.  Returns
+// the histogram words needed in *hwords.
 static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec& sp, bool pairs, uint32_t K,
                             DevSeg* hs, std::vector<uint2>& items, uint64_t* hwords) {
   std::vector<uint2> post;
@@ -420,7 +436,7 @@ static ms_status build_work(const ms_segment* segs, uint32_t num, const DevSpec&
       hw += (uint64_t)sp.m * d.C;
       for (uint32_t t = 0; t < d.L; t += K) items.push_back(make_uint2(i, t));
     }
-    for (uint32_t t = 0; t < d.L; t += K) post.push_back(make_uint2(i, t));
+    for (uint32_t t = 0; t < d.L; t += K) post.push_back(make_uint2(i, t | kBatchPost));
     hs[i] = d;
   }
   const uint32_t n_hist = (uint32_t)(items.size() - 1);

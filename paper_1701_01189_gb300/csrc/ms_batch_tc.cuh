@@ -2,17 +2,19 @@
 // 32 buckets, solving each tile with the per-thread bucket counters of
 // ms_tc.cuh.
 //
-// Same work list and protocol as k_batch: histogram items of multi-tile
-// segments first (tile histogram -> column of the segment's H; the CTA that
-// finishes a segment's last histogram scans its H and raises the ready flag),
-// then one post-scan item per tile.  Differences: a histogram item only
-// counts (one shared atomic per key, no ranks), and every CTA copies the next
-// item's tile into the other of two shared-memory slots with asynchronous
-// asynchronous copies while it works on the current one (16-byte copies
-// for the chunks of any segment phase, see copy_tile_shifted).  Items
-// are taken by ticket, three tickets ahead of the current item; a waiting
-// post-scan item only waits for histogram items, whose tickets are all
-// smaller and whose holders never wait, so every wait ends.
+// Same work list and protocol as k_batch, with items of up to K tiles:
+// histogram items of multi-tile segments first (chunk histogram -> column of
+// the segment's H; the CTA that finishes a segment's last histogram scans its
+// H and raises the ready flag), then the post-scan items.  Differences: a
+// histogram item only counts (one shared atomic per key, no ranks), reading
+// its keys straight from global memory with 16-byte loads at any segment
+// phase; a post-scan item walks its tiles in order, each CTA copying the next
+// tile -- of the same item, or the next item's first -- into the other of two
+// shared-memory slots with asynchronous copies while it works on the current
+// one (16-byte copies for the chunks of any segment phase, see
+// copy_tile_shifted).  Items are taken by ticket, three tickets ahead of the
+// current item; a waiting post-scan item only waits for histogram items of
+// smaller tickets, which never wait, so every wait ends.
 #pragma once
 
 #include "ms_tc.cuh"
@@ -118,30 +120,80 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
   for (uint32_t i = t; i < R * kTcRow; i += kTcThreads) s_cnt[i] = 0u;
   tc_build_tables<KIND>(sp, lb, lw, s_tbl, s_lut);  // ends with a barrier
   const uint2 counts = a.items[0];  // read from memory so a captured graph follows later updates
-  const uint32_t n_hist = counts.x, n_items = counts.y;
+  const uint32_t n_items = counts.y;
+  const uint64_t pol_last = policy_evict_last();
 
-  // all threads: copy tile t0 + j of item `it` (keys; values for a
-  // key-value post-scan) into `slot`, laid out as ms_tc.cuh's swizzled
-  // tiles; one commit group per call, empty or not
+  // all threads: copy tile t0 + j of post-scan item `it` (keys, and values
+  // for pairs) into `slot`, laid out as ms_tc.cuh's swizzled tiles; one
+  // commit group per call, empty or not (histogram items read their keys
+  // straight from global memory)
   auto fetch = [&](uint32_t it, uint32_t j, uint32_t slot) {
     if (it < n_items) {
       const uint2 item = a.items[1 + it];
-      const DevSeg sg = a.segs[item.x];
-      const size_t tb = (size_t)(item.y + j) * T;
-      const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
-      uint32_t* sk = smem + slot * SW;
-      copy_tile_shifted(sk, sg.kin + tb, tile_n);
-      if (PAIRS && it >= n_hist) copy_tile_shifted(sk + Lay::kRegion, sg.vin + tb, tile_n);
+      if (item.y & kBatchPost) {
+        const DevSeg sg = a.segs[item.x];
+        const size_t tb = (size_t)((item.y & ~kBatchPost) + j) * T;
+        const uint32_t tile_n = (size_t)sg.n > tb ? (uint32_t)min((size_t)T, (size_t)sg.n - tb) : 0u;
+        uint32_t* sk = smem + slot * SW;
+        copy_tile_shifted(sk, sg.kin + tb, tile_n);
+        if constexpr (PAIRS) copy_tile_shifted(sk + Lay::kRegion, sg.vin + tb, tile_n);
+      }
     }
     cp_async_commit();
+  };
+
+  // histogram item: the n keys at src (any 4-byte phase) into this thread's
+  // (bucket, thread) counters -- the 16-byte chunks inside the tile by
+  // 16-byte loads, the at most 3 words before the first chunk and after the
+  // last by 4-byte loads (measured on GB300: the next tile's loads in flight
+  // while one is counted made the batched run 1.6% slower)
+  auto count_tile = [&](const uint32_t* src, uint32_t n) {
+    const uint32_t r = (uint32_t)(reinterpret_cast<uintptr_t>(src) >> 2) & 3u;
+    const uint32_t h = min(n, (4u - r) & 3u);
+    const uint32_t nch = (n - h) >> 2;  // at most T / 4 = 4 * kTcThreads
+    uint32_t key[16], bk[16];
+    uint32_t valid = 0;  // bit i: key[i] is a key of the tile
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t k = t + kTcThreads * j;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (k < nch) {
+        v = ldg_v4_policy(src + h + 4u * k, pol_last);
+        valid |= 0xfu << (4 * j);
+      }
+      key[4 * j + 0] = v.x;
+      key[4 * j + 1] = v.y;
+      key[4 * j + 2] = v.z;
+      key[4 * j + 3] = v.w;
+    }
+    uint32_t flag = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bk[i] = tc_bucket<KIND>(key[i], sp, L, flag);
+    if constexpr (KIND == kRange)
+      if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if ((valid >> i) & 1u) atomicAdd(my + bk[i] * kTcRow, 1u);
+    const uint32_t tail0 = h + 4u * nch;
+    const bool head = t < h, tail = t >= 4u && t - 4u < n - tail0;
+    if (head || tail) {
+      const uint32_t u = src[head ? t : tail0 + (t - 4u)];
+      uint32_t f = 0;
+      uint32_t b = tc_bucket<KIND>(u, sp, L, f);
+      if constexpr (KIND == kRange)
+        if (f & kTcLutFlag) b = range_search<5>(u, s_tbl, m);
+      atomicAdd(my + b * kTcRow, 1u);
+    }
   };
 
   // Tickets are taken three items ahead, and the descriptors of the later
   // items are pulled into L1 in two steps (the item entry, then the segment
   // it names) while the current item is worked on, so that the copy of the
   // next item's first tile starts without waiting on their loads.  (Holding
-  // unstarted tickets is safe: a CTA holds histogram tickets only while it
-  // works on a histogram item, which never waits.)
+  // unstarted tickets is safe: a blocked CTA's current item waits only for
+  // histogram items of smaller tickets, and the CTA holding one of those is
+  // either working on it or blocked on a still smaller ticket, so the CTA
+  // with the smallest blocked ticket can always proceed.)
   auto prefetch_l1 = [](const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); };
   if (t == 0) {
     s_tk[0] = atomicAdd(a.ticket, 1u);
@@ -152,20 +204,40 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
   }
   __syncthreads();
   uint32_t cur = s_tk[0], nxt = s_tk[1], nxt2 = s_tk[2];
-  uint32_t slot = 0;
+  uint32_t slot = 0;  // where the next post-scan tile is (being) copied
   fetch(cur, 0, 0);
 
   while (cur < n_items) {
     const uint2 item = a.items[1 + cur];
-    const uint32_t seg = item.x, t0 = item.y;
+    const uint32_t seg = item.x, t0 = item.y & ~kBatchPost;
     const DevSeg sg = a.segs[seg];
     const uint32_t t1 = min(t0 + a.K, sg.L), chunk = t0 / a.K;
-    const bool hist = cur < n_hist;
+    const bool hist = (item.y & kBatchPost) == 0u;
     uint32_t nn = 0;    // the ticket taken during this item
     uint32_t grun = 0;  // post-scan, thread b < m: global position of bucket b's next key of this chunk
 
     for (uint32_t tile = t0; tile < t1; ++tile) {
       const bool last = tile + 1u == t1;
+      if (hist) {
+        // (A) this tile's keys into the chunk's per-thread counts; at the
+        // chunk's last tile, the next item's first tile into `slot`, free
+        // since the last post-scan tile (in the other slot) was written out
+        if (last) {
+          __syncthreads();  // everyone read s_tk[3]
+          if (t == 0) {
+            if (nxt2 < n_items) prefetch_l1(a.segs + a.items[1 + nxt2].x);
+            const uint32_t tk = atomicAdd(a.ticket, 1u);
+            s_tk[3] = tk;
+            if (tk < n_items) prefetch_l1(a.items + 1 + tk);
+          }
+          fetch(nxt, 0, slot);
+          __syncthreads();
+          nn = s_tk[3];
+        }
+        const size_t tb = (size_t)tile * T;
+        count_tile(sg.kin + tb, (uint32_t)min((size_t)T, (size_t)sg.n - tb));
+        continue;
+      }
       __syncthreads();  // the other slot's tile is written out; everyone read s_tk[3]
       if (last) {
         if (t == 0) {
@@ -196,12 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_batch_tc(BatchArgs a, uint32_
       if constexpr (KIND == kRange)
         if (flag & kTcLutFlag) tc_fixup<16>(key, bk, L, s_tbl, m);
 
-      if (hist) {
-        // (A) this tile's keys into the chunk's per-thread counts
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (16u * t + i < tile_n) atomicAdd(my + bk[i] * kTcRow, 1u);
-      } else {
+      {
         // (B) post-scan of one tile
         uint32_t val[PAIRS ? 16 : 1], pos[16];
         if constexpr (PAIRS)
