@@ -90,12 +90,18 @@ static cudaError_t launch_prescan(const Call& c, DeviceCtx& ctx, const Chunking&
   const uint32_t keep = (uint32_t)std::min<size_t>(ch.K, (keep_tiles + ch.G - 1) / ch.G);
   TcPreArgs pa{c.keys_in, c.n, ch.K, ch.L, ch.G, ch.K - keep, vec ? 1u : 0u, H, hsb, hsc, tot, lb, lw, c.sp};
   static LaunchInfo li[3];
-  // one CTA per chunk, or, when the chunks outnumber the CTAs the SMs hold at
-  // once, one wave of those CTAs, each an equal run of tiles
+  // one CTA per chunk; or, when the chunks outnumber the CTAs the SMs hold at
+  // once, or number at most half of them (a post-scan of one CTA per SM),
+  // one wave of those CTAs, each an equal run of tiles whose pieces add into
+  // their chunks' columns of H (measured on GB300: key-value multisplits of
+  // 2^26 elements with 256 buckets had their pre-scan at one CTA per SM,
+  // 26-47% slower than for the same keys alone)
   auto launch = [&](auto k, size_t smem, size_t smem_max, LaunchInfo& info) {
     const int resident = setup_kernel(info, k, kTcThreads, smem_max, smem, ctx.device);
-    const uint32_t grid = std::max(1u, std::min(ch.G, (uint32_t)(ctx.sm_count * resident)));
-    k<<<grid, kTcThreads, smem, c.stream>>>(pa);
+    const uint32_t cap = (uint32_t)(ctx.sm_count * resident);
+    uint32_t grid = std::min(ch.G, cap);
+    if (2u * ch.G <= cap) grid = std::min(cap, ch.L);
+    k<<<std::max(1u, grid), kTcThreads, smem, c.stream>>>(pa);
   };
   if (mode == kCountLaneBytes)
     launch(k_prescan_tc<KIND, kCountLaneBytes>, tc_prescan_smem<KIND, kCountLaneBytes>(m, lb, lw),

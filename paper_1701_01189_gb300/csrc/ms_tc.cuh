@@ -226,9 +226,18 @@ __host__ __device__ constexpr int tc_prescan_depth() {
   return (KIND == kRange && MODE != kCountLaneBytes) ? 3 : 2;
 }
 
+// CTAs per SM the pre-scan is compiled for: two where a third tile in flight
+// (range buckets, up to 32 of them) or the range lookup of the byte counters
+// (more than 32 buckets: it spills at 80 registers) needs the registers,
+// three otherwise (measured on GB300, 2^26 keys: delta buckets, 64 of them,
+// 92 -> 78 us; 256 of them, 99 -> 88 us).
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(kTcThreads, (MODE == kCountLaneBytes || tc_prescan_depth<KIND, MODE>() == 3) ? 2 : 3)
-    k_prescan_tc(TcPreArgs a) {
+__host__ __device__ constexpr int tc_prescan_min_ctas() {
+  return (tc_prescan_depth<KIND, MODE>() == 3 || (MODE == kCountLaneBytes && KIND == kRange)) ? 2 : 3;
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(kTcThreads, tc_prescan_min_ctas<KIND, MODE>()) k_prescan_tc(TcPreArgs a) {
   constexpr int BB = MODE == kCountLaneBytes ? 8 : 5;  // bits of a bucket in the lookup table
   constexpr int NW = kTcThreads / 32;
   extern __shared__ __align__(16) uint32_t smem[];

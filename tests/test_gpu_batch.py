@@ -11,7 +11,9 @@ from parity import Case, clustered_splitters, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [0, 1, 31, 4095, 4096, 4097, 10000, 3 * 4096 + 5, 70000, 255, 2]
+# 0 to several tiles of 4096 keys; 8 and 9 tiles and 70000 (18 tiles) cross
+# the 8-tile work items of the per-thread-counter batched kernel
+SIZES = [0, 1, 31, 4095, 4096, 4097, 10000, 3 * 4096 + 5, 8 * 4096, 8 * 4096 + 1, 70000, 255, 2]
 
 
 def cases():
