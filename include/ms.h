@@ -133,8 +133,8 @@ ms_status ms_histogram(const uint32_t *keys, size_t n, const ms_bucket_spec *spe
  *   - The first call on each device (with it current) looks up the array's
  *     device address; the first call that uses a given kernel variant (picked
  *     by the bucket kind, m and the size class of n) sets that kernel's
- *     attributes and queries its occupancy.  Make these first calls before any
- *     stream capture.  None of this allocates.
+ *     attributes and queries its occupancy; later calls skip these host-side
+ *     steps.  None of this allocates.
  *   - All calls share the array: calls that overlap on the GPU race and
  *     corrupt each other's results; serialize them (one stream, or events).
  *   - The scratch must hold 4*m*G + 16 bytes, plus 8*ceil(m*G/4096) for

@@ -16,8 +16,8 @@
 // the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and remembers it.  The first
 // call that uses a given kernel variant (bucket kind, m and the size class of
-// n pick it) also sets that kernel's attributes and queries its occupancy.
-// Make these first calls before any stream capture.  All calls share the
+// n pick it) also sets that kernel's attributes and queries its occupancy;
+// later calls skip these host-side steps.  All calls share the
 // array: calls that overlap on the GPU (concurrent streams, or several
 // devices' worth of work racing on one device) race on it and corrupt each
 // other; serialize them.  Each call clears the words that must start at zero
