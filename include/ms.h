@@ -183,8 +183,9 @@ typedef struct ms_batch_plan ms_batch_plan;
 
 /* Reads the host array segs[num_segments] (copied; the device buffers it
  * names must stay valid while the plan is used, as must spec->splitters) and
- * builds the work list: one item per 4096-key tile for the tile histograms of
- * segments longer than one tile, one per tile for the post-scans.  Allocates
+ * builds the work list: items of up to 8 consecutive 4096-key tiles of one
+ * segment (one tile for the kernel of more than 32 buckets), first for the
+ * histograms of segments longer than one tile, then for the post-scans.  Allocates
  * the plan's device memory with cudaMalloc and uploads the list
  * (synchronous; do it once, outside any capture).  The plan is key-value if
  * any segment has vals_in; every non-empty segment must then carry values.
